@@ -1,0 +1,368 @@
+#!/usr/bin/env python3
+"""Benchmark of the implicit ADI wave-equation hot path on GB300.
+
+One bench step = one pass of the hot path over one synthetic problem: the
+start-up (Eq. CN2) followed by the workload's ADI time steps (RHS assembly,
+x sweep, y sweep + update, Algorithm 1's loop), with every input resident in
+HBM.  The default workload is the 16384 x 16384 bandwidth case: seeded
+heterogeneous c-field, Ricker point source, tau = 0.5 h / max c, 200 time
+steps, four FP32 fields of 1 GiB each resident (far larger than L2, so no
+flush is needed between steps).
+
+Prints ONE JSON line (rank 0).  `value` is whole-job grid-point updates per
+second over the timed region (CUDA events on the launching stream, max over
+ranks); `e2e` is the same metric through the public API from pinned host
+buffers (H2D of m and phi, D2H of the final field inside the timed region);
+`roofline` reports the dominant kernel's algorithmic HBM bytes per launch over
+its average event-timed duration against the measured copy bandwidth;
+`cpu_baseline` is the FP64 oracle timed on the host cores on a bounded sample
+of the same workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload ricker_16384|ricker_4096|standing_wave_128]
+Under torchrun (N > 1) every rank runs its own replica of the workload on its
+own GPU (the single grid does not shard; the batched form shards by shot).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    "ricker_16384": dict(n=16384, time_steps=200, kind="ricker"),
+    "ricker_4096": dict(n=4096, time_steps=1000, kind="ricker"),
+    "standing_wave_128": dict(n=128, time_steps=200, kind="standing"),
+}
+METRIC = "ADI grid-point updates/sec"
+UNIT = "grid-point updates/s"
+# algorithmic HBM bytes per grid point per launch (FP32 fields)
+BYTES_X = 12  # read u^k, m; write w
+BYTES_Y = 20  # read w, m, u^k, u^{k-1}; write u^{k+1}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from the ncu capture
+# summarised in profiles/ (None until measured for the current kernels)
+NCU_TRAFFIC = {}
+
+
+def measured_peak_gbs():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() in ("active", "1", "0x1"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def make_problem(wl):
+    from paper_2006_10142_gb300 import inputs
+    n, ts = wl["n"], wl["time_steps"]
+    if wl["kind"] == "standing":
+        p = inputs.standing_wave_problem(n, ts)
+        p.m = p.m.astype(np.float32)
+        p.phi = p.phi.astype(np.float32)
+        return p
+    return inputs.ricker_problem(n, ts, seed=0, m_dtype=np.float32)
+
+
+def cpu_baseline(prob, wl, budget_s=15.0):
+    """FP64 oracle on the host cores, on a bounded sample: the workload's grid,
+    a few of its time steps from the same start (steps scaled to the budget)."""
+    import oracle
+    threads = os.cpu_count() or 1
+    n = wl["n"]
+    m64 = prob.m.astype(np.float64)
+    phi64 = prob.phi.astype(np.float64)
+    hx = 1.0 / (n + 1)
+    u0, u1 = oracle.adi_init(m64, phi64, hx, hx, prob.tau)
+    wav = prob.wavelet.astype(np.float32).astype(np.float64) if prob.wavelet is not None else None
+    t0 = time.perf_counter()
+    up, uc, _ = oracle.adi_run(m64, u0, u1, hx, hx, prob.tau, 1, k0=1, src=prob.src, wavelet=wav,
+                               threads=threads)
+    t1 = time.perf_counter() - t0
+    extra = int(max(0, min(wl["time_steps"] - 1, budget_s / max(t1, 1e-6) - 1)))
+    steps = 1
+    t_total = t1
+    if extra > 0:
+        t0 = time.perf_counter()
+        oracle.adi_run(m64, up, uc, hx, hx, prob.tau, extra, k0=2, src=prob.src, wavelet=wav,
+                       threads=threads)
+        t_total += time.perf_counter() - t0
+        steps += extra
+    return {"value": float(n * n * steps / t_total), "unit": UNIT, "cores": threads,
+            "kind": "oracle",
+            "sample": "%d of the workload's %d ADI steps on the full %dx%d grid, FP64, %d threads"
+                      % (steps, wl["time_steps"], n, n, threads)}
+
+
+def run_reference(args, wl, rank):
+    """The reference arm: the FP64 oracle as it stands, on the host cores."""
+    if rank != 0:
+        return None
+    import oracle
+    prob = make_problem(wl)
+    threads = os.cpu_count() or 1
+    n = wl["n"]
+    m64 = prob.m.astype(np.float64)
+    hx = 1.0 / (n + 1)
+    u0, u1 = oracle.adi_init(m64, prob.phi.astype(np.float64), hx, hx, prob.tau)
+    wav = prob.wavelet.astype(np.float32).astype(np.float64) if prob.wavelet is not None else None
+    # each bench step: a bounded sample of the workload (ADI steps on the full grid)
+    sample_steps = max(1, min(wl["time_steps"], int(2e8 // (n * n)) or 1))
+    state = [u0, u1, 1]
+
+    def one():
+        up, uc, k = state
+        up, uc, _ = oracle.adi_run(m64, up, uc, hx, hx, prob.tau, sample_steps, k0=k,
+                                   src=prob.src, wavelet=wav, threads=threads)
+        state[0], state[1], state[2] = up, uc, k + sample_steps
+
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    dt = time.perf_counter() - t0
+    val = n * n * sample_steps * args.steps / dt
+    sample = ("%d ADI steps of the %dx%d grid per bench step (of the workload's %d), FP64, %d threads"
+              % (sample_steps, n, n, wl["time_steps"], threads))
+    return {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": args.workload, "n": n, "time_steps": wl["time_steps"]},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ricker_16384", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        out = run_reference(args, wl, rank)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2006_10142_gb300 import api
+
+    n, ts = wl["n"], wl["time_steps"]
+    prob = make_problem(wl)
+    m_d = torch.from_numpy(prob.m).to(dev)
+    phi_d = torch.from_numpy(prob.phi.astype(np.float32)).to(dev)
+    src = prob.src
+    wav_d = torch.from_numpy(prob.wavelet.astype(np.float32)).to(dev) if prob.wavelet is not None else None
+    h = api.AdiWave(m_d, phi_d, prob.tau, src=src, wavelet=wav_d)
+
+    def bench_step():
+        h.reset(phi_d)
+        h.run(ts, src=src, wavelet=wav_d)
+
+    for _ in range(max(args.warmup, 0)):
+        bench_step()
+    h.sync_status()
+    stream = torch.cuda.current_stream()
+    h.profile(True)
+    h.profile_read()
+    clocks = ClockSampler(torch.cuda.get_device_properties(dev).uuid if hasattr(
+        torch.cuda.get_device_properties(dev), "uuid") else local_rank)
+    if rank == 0:
+        clocks.start()
+        time.sleep(0.5)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = h.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        bench_step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = h.launch_count() - l0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop() if rank == 0 else None
+    elapsed_ms = ev0.elapsed_time(ev1)
+    kms, kcnt = h.profile_read()
+    h.profile(False)
+    h.sync_status()
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    value = world * n * n * ts * args.steps / (max_ms / 1e3)
+
+    # roofline of the dominant kernel
+    peak, peak_kind = measured_peak_gbs()
+    kind = 0 if kms[0] >= kms[1] else 1
+    name = "x_sweep_kernel" if kind == 0 else "y_sweep_kernel"
+    per_launch_ms = kms[kind] / max(kcnt[kind], 1)
+    alg_bytes = (BYTES_X if kind == 0 else BYTES_Y) * n * n
+    achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
+    traffic = NCU_TRAFFIC.get((name, args.workload))
+
+    # end to end through the public API from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        m_h = torch.from_numpy(prob.m).pin_memory()
+        phi_h = torch.from_numpy(prob.phi.astype(np.float32)).pin_memory()
+        wav_h = (torch.from_numpy(prob.wavelet.astype(np.float32)).pin_memory()
+                 if prob.wavelet is not None else None)
+        out_h = torch.empty((n, n), dtype=torch.float32).pin_memory()
+        m_s = torch.empty_like(m_d)
+        phi_s = torch.empty_like(phi_d)
+        wav_s = torch.empty_like(wav_d) if wav_d is not None else None
+
+        def e2e_step():
+            m_s.copy_(m_h, non_blocking=True)
+            phi_s.copy_(phi_h, non_blocking=True)
+            if wav_s is not None:
+                wav_s.copy_(wav_h, non_blocking=True)
+            h.reset(phi_s, m=m_s)
+            h.run(ts, src=src, wavelet=wav_s)
+            _, uc, _ = h.state()
+            out_h.copy_(uc, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e_dt = time.perf_counter() - t0
+        te = torch.tensor([e_dt], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        bi = m_h.numel() * 4 + phi_h.numel() * 4 + (wav_h.numel() * 4 if wav_h is not None else 0)
+        e2e = {"value": world * n * n * ts * args.steps / float(te.item()), "unit": UNIT,
+               "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(n * n * 4)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(prob, wl)
+
+    if rank == 0:
+        tun = h.tuning()
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "time_steps": ts,
+                       "medium": "seeded c-field 1 + 2 sigmoid(8 Gaussian bumps), m = c^2",
+                       "source": "Ricker f=20" if wl["kind"] == "ricker" else "none",
+                       "l2": "inputs larger than L2 (4 FP32 fields of %.0f MiB)" % (n * n * 4 / 2**20),
+                       "timed_launches": "direct launches with per-kernel CUDA events",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "tuning": tun},
+            "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                         "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
+                         "avg_launch_ms": per_launch_ms,
+                         "kernel_ms": {"x_sweep_kernel": kms[0], "y_sweep_kernel": kms[1]},
+                         "kernel_launches": {"x_sweep_kernel": kcnt[0], "y_sweep_kernel": kcnt[1]},
+                         "step_gbs_32B": 32.0 * n * n * ts * args.steps / (max_ms / 1e3) / 1e9},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out), flush=True)
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,229 @@
+/*
+ * adiwave.h -- C ABI of libadiwave.so, the GB300 (sm_103a) implementation of
+ * the implicit ADI scheme for the 2D acoustic wave equation of Altybay,
+ * Ruzhansky and Tokmagambetov, "A parallel hybrid implementation of the 2D
+ * acoustic wave equation".
+ *
+ * Problem (Section 2, Eqs. f1-f5): u_tt - m (u_xx + u_yy) = f on
+ * [0,T] x [0,lx] x [0,ly], u = phi and u_t = psi at t = 0, u = 0 on the
+ * boundary.  The coefficient that multiplies the Laplacian is passed as
+ * m = c^2 (c is the wave speed) and does not depend on time.
+ *
+ * Grid (Eq. f6): nx x ny interior nodes, h1 = lx / (nx + 1),
+ * h2 = ly / (ny + 1); node (i, j), 0 <= i < nx, 0 <= j < ny, sits at
+ * ((i + 1) h1, (j + 1) h2).  The Dirichlet ring (Eq. CN3) is implicit and
+ * never stored.  Every field crossing this ABI is FP32, row-major
+ * [ny][nx] with x fastest, contiguous (row stride nx), in DEVICE memory
+ * unless stated otherwise.
+ *
+ * Time stepping: the Crank-Nicolson three-level scheme of Eq. (CN1) in
+ * delta form, (I - S Lap) z = tau^2 (m Lap u^k + f^k), z = u^{k+1} - 2u^k +
+ * u^{k-1}, S = diag(tau^2 m / 2), with the ADI factorisation of Section 2
+ * (sub-problems Eqs. fr1 and fr2): a tridiagonal sweep along x per row,
+ * then one along y per column, each solved on the GPU by a per-thread
+ * partition step followed by cyclic reduction of the interface system and
+ * warp-shuffle parallel cyclic reduction for its last levels (Section 3.1
+ * solves the same systems by cyclic reduction).
+ *
+ * Point source: f^k = w(t_k) / (h1 h2) at one node (a delta-like datum
+ * approximated on the grid, Section 2).  Time level k uses the sample
+ * wavelet[k], t_k = k tau.
+ *
+ * Streams and ordering: every call enqueues its work on the CUDA stream it
+ * is given (a cudaStream_t passed as void*, NULL = legacy default stream)
+ * and returns without waiting for the GPU, unless stated otherwise.  Device
+ * buffers passed in must stay valid until the work that reads or writes
+ * them has completed in stream order.
+ *
+ * Errors: every int-returning call returns ADI_OK (0) or one of the
+ * ADI_E* codes below; no C++ exception and no abort crosses the ABI.
+ * Conditions found on the GPU (non-finite values, an expired bounded wait)
+ * are recorded in a device error word and reported by
+ * adi_wave_sync_status().  adi_wave_strerror() turns a code into text and
+ * adi_wave_last_error() gives the detail of the last failure on a handle.
+ *
+ * Threads: a handle may be used by one host thread at a time.
+ */
+#ifndef ADIWAVE_H
+#define ADIWAVE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    ADI_OK = 0,
+    ADI_EINVAL = 1,      /* invalid argument (null pointer, size, index, mode) */
+    ADI_ENOMEM = 2,      /* device or host allocation failed */
+    ADI_ECUDA = 3,       /* a CUDA runtime call failed */
+    ADI_ENUMERIC = 4,    /* a non-finite value was produced (device flag) */
+    ADI_ETIMEOUT = 5,    /* a bounded device-side wait expired (device flag) */
+    ADI_ESTATE = 6,      /* call not valid in the handle's state */
+    ADI_EUNSUPPORTED = 7 /* valid request this build does not implement */
+};
+
+enum { ADI_START_PAPER = 0,     /* Eq. (CN2): u^1 = phi + tau psi */
+       ADI_START_TAYLOR2 = 1 }; /* u^1 = phi + tau psi + tau^2/2 (m Lap phi + f^0) */
+
+enum { ADI_FP64_AUTO = 0,   /* FP64 elimination only where diagonal dominance is weak */
+       ADI_FP64_NEVER = 1,  /* always FP32 elimination */
+       ADI_FP64_ALWAYS = 2  /* always FP64 elimination (FP32 storage) */ };
+
+typedef struct adi_wave adi_wave; /* opaque; owned by the library */
+
+/* One grid.  nx, ny >= 1 (at most 32768 each); lx, ly > 0; dt = tau > 0. */
+typedef struct {
+    int32_t nx, ny;
+    double lx, ly;
+    double dt;
+    int32_t start;      /* ADI_START_* */
+    int32_t fp64_solve; /* ADI_FP64_* */
+} adi_wave_desc;
+
+/* Point source of one grid.  ix < 0 means "no source".  wavelet is a device
+ * array of n_wavelet FP32 samples, wavelet[k] = w(t_k); levels k >=
+ * n_wavelet get w = 0.  The array is borrowed: it must stay valid while
+ * work that reads it is in flight, and until adi_wave_adjoint() returns if
+ * the run is later differentiated. */
+typedef struct {
+    int32_t ix, iy;
+    const float *wavelet;
+    int32_t n_wavelet;
+} adi_source;
+
+/* Create a handle for n_shots independent grids (n_shots == 1: one grid;
+ * n_shots > 1: the batched form that advances all grids together, one
+ * persistent kernel launch per sweep and step).
+ *   desc[s]      grid of shot s (host array of n_shots).
+ *   m[s]         device pointer, [ny][nx] FP32 coefficient m = c^2 > 0.
+ *   phi[s]       device pointer, [ny][nx] FP32 initial value u(0).
+ *   psi          host array of n_shots device pointers to u_t(0), or NULL;
+ *                entries may be NULL (= 0).
+ *   src          host array of n_shots sources, or NULL; only read by the
+ *                Taylor start (f^0).
+ * The inputs are copied into library-owned device memory (row pitch padded
+ * to 32 floats) in stream order; the caller may free them once the stream
+ * has passed this call.  After init the handle holds u^0 and u^1 (time
+ * level k = 1), Eq. (CN2).  Returns ADI_EINVAL for a bad size or pointer,
+ * ADI_ENOMEM if device memory runs out (nothing is leaked, *out = NULL). */
+int adi_wave_init(adi_wave **out, const adi_wave_desc *desc, int32_t n_shots,
+                  const float *const *m, const float *const *phi,
+                  const float *const *psi, const adi_source *src,
+                  void *stream);
+
+/* Re-run the start-up of Eq. (CN2) in place on an existing handle: copy new
+ * coefficients m (may be NULL = keep), initial data phi (and psi, may be
+ * NULL) of every shot, set the level back to k = 1 and forget the recorded
+ * run.  Same pointer conventions as adi_wave_init; allocates nothing. */
+int adi_wave_reset(adi_wave *h, const float *const *m, const float *const *phi,
+                   const float *const *psi, const adi_source *src, void *stream);
+
+/* Advance every grid by one time step (u^{k-1}, u^k -> u^k, u^{k+1}),
+ * Algorithm 1's loop body.  src: host array of n_shots sources or NULL. */
+int adi_wave_step(adi_wave *h, const adi_source *src, void *stream);
+
+/* Advance by `steps` time steps (Algorithm 1's loop).  The steps of a
+ * single grid are replayed from a captured CUDA graph.
+ *   src      host array of n_shots sources or NULL.
+ *   rec_xy   HOST array [n_rec][2] of receiver nodes (ix, iy) of shot 0, or
+ *            NULL with n_rec = 0; receivers need n_shots == 1.
+ *   traces   device [steps][n_rec] FP32: traces[s][r] = u^{k0+s+1}(rec r),
+ *            k0 the level at the call; NULL allowed when n_rec = 0.
+ * The run is remembered (start state, steps, source, receivers) so that
+ * adi_wave_adjoint() can differentiate it; with checkpointing enabled
+ * (adi_wave_set_checkpointing) the states every `every` steps are kept. */
+int adi_wave_run(adi_wave *h, int32_t steps, const adi_source *src,
+                 const int32_t *rec_xy, int32_t n_rec, float *traces,
+                 void *stream);
+
+/* Keep (u^{k-1}, u^k) every `every` steps during adi_wave_run (0 = off).
+ * The memory (2 fields per checkpoint) is allocated by the next run. */
+int adi_wave_set_checkpointing(adi_wave *h, int32_t every);
+
+/* Gradient of J = 1/2 sum_s sum_r (traces[s][r] - d[s][r])^2 for the last
+ * adi_wave_run of a single grid, given resid = traces - d (device
+ * [steps][n_rec] FP32).  The transposed x and y sweeps run backward in
+ * time; the forward fields are recomputed from checkpoints taken every
+ * ckpt_every steps (reusing the run's checkpoints when they match).
+ *   grad_m        device [ny][nx] FP64, overwritten with dJ/dm (m = c^2);
+ *                 the accumulation over steps is done in FP64.
+ *   grad_wavelet  device [n_wavelet] FP32 dJ/dw(t_k), or NULL.
+ * The handle's state (u^{k-1}, u^k) is left as it was after the run.
+ * Returns ADI_ESTATE if no single-grid run was recorded. */
+int adi_wave_adjoint(adi_wave *h, const float *resid, double *grad_m,
+                     float *grad_wavelet, int32_t ckpt_every, void *stream);
+
+/* Copy the state of shot `shot` out: u_prev = u^{k-1}, u_cur = u^k (device
+ * [ny][nx] each, either may be NULL) and *k = k (may be NULL; the level is
+ * tracked on the host, so *k is exact when the call returns). */
+int adi_wave_get_state(const adi_wave *h, int32_t shot, float *u_prev,
+                       float *u_cur, int64_t *k, void *stream);
+
+/* Replace the state of shot `shot` (device [ny][nx] each) and its level k.
+ * Clears the recorded run. */
+int adi_wave_set_state(adi_wave *h, int32_t shot, const float *u_prev,
+                       const float *u_cur, int64_t k, void *stream);
+
+/* Wait for the handle's work on `stream` and report the device error word:
+ * ADI_OK, ADI_ENUMERIC or ADI_ETIMEOUT (ADI_ECUDA if the wait failed).
+ * Clears the word.  This call blocks the host. */
+int adi_wave_sync_status(adi_wave *h, void *stream);
+
+/* Free everything the handle owns (device memory, graphs, events).  Waits
+ * for the handle's outstanding work first.  NULL is ignored. */
+void adi_wave_destroy(adi_wave *h);
+
+/* Static text for a return code. */
+const char *adi_wave_strerror(int code);
+
+/* Detail of the last failing call on h (static empty string if none). */
+const char *adi_wave_last_error(const adi_wave *h);
+
+/* ---- tuning (the autotuner's knobs) -------------------------------------
+ * chunk_x, chunk_y: rows of a line held by one thread in the partition step
+ *                   (4, 8, 16 or 32);
+ * rows_per_cta:     systems (grid rows) solved by one CTA in the x sweep;
+ * cols_per_cta:     columns of the strip one CTA (cluster) solves in the
+ *                   y sweep (8, 16 or 32);
+ * pcr_size:         size of the interface system handed from cyclic
+ *                   reduction to warp-shuffle parallel cyclic reduction
+ *                   (2, 4, 8, 16 or 32; the CR-to-PCR switch level);
+ * use_graph:        1 = replay steps from a captured CUDA graph.
+ * Zero fields mean "choose automatically". */
+typedef struct {
+    int32_t chunk_x, chunk_y;
+    int32_t rows_per_cta;
+    int32_t cols_per_cta;
+    int32_t pcr_size;
+    int32_t use_graph;
+} adi_wave_tuning;
+
+int adi_wave_get_tuning(const adi_wave *h, adi_wave_tuning *t);
+int adi_wave_set_tuning(adi_wave *h, const adi_wave_tuning *t);
+
+/* ---- measurement --------------------------------------------------------
+ * With profiling on, the single-grid forward path records a CUDA event pair
+ * around every launch of each kernel kind on the launching stream and runs
+ * without graphs.  adi_wave_profile_read() waits for the handle's work,
+ * sums the recorded durations per kind into ms[kind] and launch counts
+ * into launches[kind] for kind < n_kinds, and clears the records.  Kinds:
+ * 0 = x sweep (RHS + x solve), 1 = y sweep (+ update), 2 = other. */
+enum { ADI_KERNEL_X = 0, ADI_KERNEL_Y = 1, ADI_KERNEL_OTHER = 2, ADI_KERNEL_KINDS = 3 };
+int adi_wave_profile(adi_wave *h, int32_t enable);
+int adi_wave_profile_read(adi_wave *h, double *ms, int64_t *launches,
+                          int32_t n_kinds);
+
+/* Number of kernel launches the handle has enqueued since creation (all
+ * kinds, graph replays counted per kernel node). */
+int64_t adi_wave_launch_count(const adi_wave *h);
+
+/* Library version string, e.g. "adiwave 0.1 sm_103a". */
+const char *adi_wave_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADIWAVE_H */

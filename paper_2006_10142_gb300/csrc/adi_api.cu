@@ -1,0 +1,256 @@
+// adi_api.cu -- the C ABI of libadiwave.so (declared in include/adiwave.h):
+// handle lifetime, validation, launch planning, the time loop with CUDA
+// graph replay, state access, measurement hooks.
+//
+// Algorithm 1 (Section 3.1) keeps four buffers u, U0, Ux, Uy and swaps them
+// after every step.  Here a grid owns two state buffers -- buf[cur] = u^k,
+// buf[1-cur] = u^{k-1} -- plus one scratch field w; the y sweep writes
+// u^{k+1} over u^{k-1} and `cur` flips, which is the same rotation without
+// copies.  Two consecutive steps restore the orientation, so a captured
+// graph of one step pair is replayed for the whole loop.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/adiwave.h"
+#include "adi_internal.h"
+#include "adi_run.h"
+
+using namespace adi;
+
+namespace adi {
+
+static const char* kVersion = "adiwave 0.1 sm_103a";
+
+static int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+static int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+int fail(adi_wave* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+int cuda_fail(adi_wave* h, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(h, ADI_ECUDA, m);
+}
+
+// Launch geometry of one grid (the autotuner's knobs made concrete).
+int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
+  const double sxm = G.dt * G.dt * G.mmax / (2.0 * G.hx * G.hx);
+  const double sym = G.dt * G.dt * G.mmax / (2.0 * G.hy * G.hy);
+  // dominance ratio (|a| + |c|) / |b| = 2s / (1 + 2s); weak above 0.9
+  const bool weak_x = 2.0 * sxm / (1.0 + 2.0 * sxm) > kWeakDominance;
+  const bool weak_y = 2.0 * sym / (1.0 + 2.0 * sym) > kWeakDominance;
+  GridPlan& P = G.plan;
+  P.fp64x = G.fp64mode == ADI_FP64_ALWAYS || (G.fp64mode == ADI_FP64_AUTO && weak_x);
+  P.fp64y = G.fp64mode == ADI_FP64_ALWAYS || (G.fp64mode == ADI_FP64_AUTO && weak_y);
+
+  // ---- x sweep
+  {
+    const int maxT = P.fp64x ? 512 : 1024;
+    int K = t.chunk_x;
+    if (K == 0) K = P.fp64x ? 8 : (G.nx >= 512 ? 16 : (G.nx >= 64 ? 8 : 4));
+    if (K != 4 && K != 8 && K != 16 && K != 32) { why = "chunk_x must be 4, 8, 16 or 32"; return ADI_EINVAL; }
+    while (next_pow2((G.nx + K - 1) / K) > maxT && K < 32) K *= 2;
+    const int tsys = next_pow2((G.nx + K - 1) / K);
+    if (tsys > maxT) { why = "nx too large for one CTA per row"; return ADI_EUNSUPPORTED; }
+    int spc = t.rows_per_cta;
+    if (spc == 0) spc = std::max(1, std::min(maxT / tsys, G.ny / 304));
+    if (spc < 1 || spc * tsys > maxT) { why = "rows_per_cta too large"; return ADI_EINVAL; }
+    // whole warps only: the interface solve uses full-warp shuffles
+    if (spc * tsys < 32) spc = 32 / tsys;
+    int pcr = t.pcr_size ? t.pcr_size : 32;
+    if (pcr != 2 && pcr != 4 && pcr != 8 && pcr != 16 && pcr != 32) { why = "pcr_size must be 2..32, a power of two"; return ADI_EINVAL; }
+    if (x_smem_bytes(spc, tsys, P.fp64x) > 200 * 1024) { why = "x sweep shared memory too large"; return ADI_EUNSUPPORTED; }
+    P.kx = K;
+    P.log2tsys = ilog2(tsys);
+    P.spc = spc;
+    P.pcr = pcr;
+  }
+  // ---- y sweep
+  {
+    const int maxT = P.fp64y ? 512 : 1024;
+    int W = t.cols_per_cta ? t.cols_per_cta : 8;
+    if (W != 4 && W != 8 && W != 16 && W != 32) { why = "cols_per_cta must be 4, 8, 16 or 32"; return ADI_EINVAL; }
+    int K = t.chunk_y;
+    const int maxC = 16;
+    if (K == 0) {
+      K = P.fp64y ? 8 : (G.ny >= 64 ? 8 : 4);
+      // prefer portable clusters (<= 8 CTAs)
+      while (K < 32 && next_pow2((G.ny + K - 1) / K) / std::min(next_pow2((G.ny + K - 1) / K), maxT / W) > 8) K *= 2;
+    }
+    if (K != 4 && K != 8 && K != 16 && K != 32) { why = "chunk_y must be 4, 8, 16 or 32"; return ADI_EINVAL; }
+    const int ttot = next_pow2((G.ny + K - 1) / K);
+    int tcol = std::min(ttot, maxT / W);
+    if (W * tcol < 32) tcol = 32 / W;  // whole warps; extra chunks are empty rows
+    const int C = std::max(1, ttot / tcol);
+    if (C > maxC) { why = "ny too large for a 16-CTA cluster"; return ADI_EUNSUPPORTED; }
+    if (y_smem_bytes(W, C, tcol, P.fp64y) > 200 * 1024) { why = "y sweep shared memory too large"; return ADI_EUNSUPPORTED; }
+    P.ky = K;
+    P.log2W = ilog2(W);
+    P.log2tcol = ilog2(tcol);
+    P.C = C;
+  }
+  P.graph = (t.use_graph == 0) ? 1 : (t.use_graph > 0 ? 1 : 0);
+  return ADI_OK;
+}
+
+}  // namespace adi
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" const char* adi_wave_version(void) { return kVersion; }
+
+extern "C" const char* adi_wave_strerror(int code) {
+  switch (code) {
+    case ADI_OK: return "ok";
+    case ADI_EINVAL: return "invalid argument";
+    case ADI_ENOMEM: return "out of memory";
+    case ADI_ECUDA: return "CUDA runtime error";
+    case ADI_ENUMERIC: return "non-finite value produced";
+    case ADI_ETIMEOUT: return "bounded device wait expired";
+    case ADI_ESTATE: return "call not valid in the handle's state";
+    case ADI_EUNSUPPORTED: return "not supported by this build";
+    default: return "unknown error code";
+  }
+}
+
+extern "C" const char* adi_wave_last_error(const adi_wave* h) {
+  return h ? h->err.c_str() : "";
+}
+
+extern "C" int adi_wave_init(adi_wave** out, const adi_wave_desc* desc, int32_t n_shots,
+                             const float* const* m, const float* const* phi,
+                             const float* const* psi, const adi_source* src, void* stream) {
+  if (!out) return ADI_EINVAL;
+  *out = nullptr;
+  if (!desc || n_shots < 1 || !m || !phi) return ADI_EINVAL;
+  for (int s = 0; s < n_shots; ++s) {
+    const adi_wave_desc& d = desc[s];
+    if (d.nx < 1 || d.ny < 1 || d.nx > 32768 || d.ny > 32768) return ADI_EINVAL;
+    if (!(d.lx > 0) || !(d.ly > 0) || !(d.dt > 0) || !std::isfinite(d.dt)) return ADI_EINVAL;
+    if (d.start != ADI_START_PAPER && d.start != ADI_START_TAYLOR2) return ADI_EINVAL;
+    if (d.fp64_solve < ADI_FP64_AUTO || d.fp64_solve > ADI_FP64_ALWAYS) return ADI_EINVAL;
+    if (!m[s] || !phi[s]) return ADI_EINVAL;
+    if (src && src[s].ix >= 0 &&
+        (src[s].ix >= d.nx || src[s].iy < 0 || src[s].iy >= d.ny)) return ADI_EINVAL;
+  }
+  adi_wave* h = new (std::nothrow) adi_wave();
+  if (!h) return ADI_ENOMEM;
+  int rc = h->create(desc, n_shots, m, phi, psi, src, (cudaStream_t)stream);
+  if (rc != ADI_OK) {
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return ADI_OK;
+}
+
+extern "C" int adi_wave_reset(adi_wave* h, const float* const* m, const float* const* phi,
+                              const float* const* psi, const adi_source* src, void* stream) {
+  if (!h || !phi) return ADI_EINVAL;
+  return h->reset(m, phi, psi, src, (cudaStream_t)stream);
+}
+
+extern "C" int adi_wave_step(adi_wave* h, const adi_source* src, void* stream) {
+  if (!h) return ADI_EINVAL;
+  return h->run(1, src, nullptr, 0, nullptr, (cudaStream_t)stream, /*record=*/false);
+}
+
+extern "C" int adi_wave_run(adi_wave* h, int32_t steps, const adi_source* src,
+                            const int32_t* rec_xy, int32_t n_rec, float* traces, void* stream) {
+  if (!h) return ADI_EINVAL;
+  return h->run(steps, src, rec_xy, n_rec, traces, (cudaStream_t)stream, /*record=*/true);
+}
+
+extern "C" int adi_wave_set_checkpointing(adi_wave* h, int32_t every) {
+  if (!h || every < 0) return ADI_EINVAL;
+  h->ckpt_every = every;
+  return ADI_OK;
+}
+
+extern "C" int adi_wave_adjoint(adi_wave* h, const float* resid, double* grad_m,
+                                float* grad_wavelet, int32_t ckpt_every, void* stream) {
+  if (!h) return ADI_EINVAL;
+  return h->adjoint(resid, grad_m, grad_wavelet, ckpt_every, (cudaStream_t)stream);
+}
+
+extern "C" int adi_wave_get_state(const adi_wave* h, int32_t shot, float* u_prev, float* u_cur,
+                                  int64_t* k, void* stream) {
+  if (!h || shot < 0 || shot >= (int)h->g.size()) return ADI_EINVAL;
+  const Grid& G = h->g[shot];
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t wb = sizeof(float) * (size_t)G.nx;
+  if (u_prev) {
+    cudaError_t e = cudaMemcpy2DAsync(u_prev, wb, G.buf[1 - G.cur], sizeof(float) * G.ld, wb, G.ny,
+                                      cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(const_cast<adi_wave*>(h), e, "get_state");
+  }
+  if (u_cur) {
+    cudaError_t e = cudaMemcpy2DAsync(u_cur, wb, G.buf[G.cur], sizeof(float) * G.ld, wb, G.ny,
+                                      cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(const_cast<adi_wave*>(h), e, "get_state");
+  }
+  if (k) *k = G.k;
+  return ADI_OK;
+}
+
+extern "C" int adi_wave_set_state(adi_wave* h, int32_t shot, const float* u_prev,
+                                  const float* u_cur, int64_t k, void* stream) {
+  if (!h || shot < 0 || shot >= (int)h->g.size() || !u_prev || !u_cur) return ADI_EINVAL;
+  return h->set_state(shot, u_prev, u_cur, k, (cudaStream_t)stream);
+}
+
+extern "C" int adi_wave_sync_status(adi_wave* h, void* stream) {
+  if (!h) return ADI_EINVAL;
+  return h->sync_status((cudaStream_t)stream);
+}
+
+extern "C" void adi_wave_destroy(adi_wave* h) { delete h; }
+
+extern "C" int adi_wave_get_tuning(const adi_wave* h, adi_wave_tuning* t) {
+  if (!h || !t) return ADI_EINVAL;
+  const GridPlan& P = h->g[0].plan;
+  t->chunk_x = P.kx;
+  t->chunk_y = P.ky;
+  t->rows_per_cta = P.spc;
+  t->cols_per_cta = 1 << P.log2W;
+  t->pcr_size = P.pcr;
+  t->use_graph = P.graph ? 1 : -1;
+  return ADI_OK;
+}
+
+extern "C" int adi_wave_set_tuning(adi_wave* h, const adi_wave_tuning* t) {
+  if (!h || !t) return ADI_EINVAL;
+  return h->set_tuning(*t);
+}
+
+extern "C" int adi_wave_profile(adi_wave* h, int32_t enable) {
+  if (!h) return ADI_EINVAL;
+  h->profile = enable != 0;
+  return ADI_OK;
+}
+
+extern "C" int adi_wave_profile_read(adi_wave* h, double* ms, int64_t* launches, int32_t n_kinds) {
+  if (!h || n_kinds < 0) return ADI_EINVAL;
+  return h->profile_read(ms, launches, n_kinds);
+}
+
+extern "C" int64_t adi_wave_launch_count(const adi_wave* h) { return h ? h->launches : 0; }

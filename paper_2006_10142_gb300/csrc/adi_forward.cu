@@ -1,0 +1,424 @@
+// adi_forward.cu -- forward-step kernels of the factored ADI scheme.
+//
+// One time step (Eq. CN1 in delta form, factored as in Section 2):
+//   pass 1, x_sweep_kernel: r = tau^2 (m Lap u^k + f^k) fused with the row
+//           solves X w = r, X = I - S Lap_x (Eq. fr1's operator);
+//   pass 2, y_sweep_kernel: the column solves Y z = w, Y = I - S Lap_y
+//           (Eq. fr2's operator), fused with u^{k+1} = 2u^k - u^{k-1} + z,
+//           written over u^{k-1} (the buffer swap of Algorithm 1).
+// Both solve their lines with the partition + CR + PCR scheme of
+// adi_device.cuh.  Memory traffic per grid point: pass 1 reads u^k and m
+// and writes w (12 B, plus halo rows served by L2); pass 2 reads w, m, u^k,
+// u^{k-1} and writes u^{k+1} (20 B).
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "adi_device.cuh"
+#include "adi_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace adi {
+
+template <int K>
+__device__ __forceinline__ void load_vec(float (&v)[K], const float* __restrict__ p) {
+  const float4* p4 = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int q = 0; q < K / 4; ++q) {
+    float4 t = __ldg(p4 + q);
+    v[4 * q + 0] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+  }
+}
+
+template <int K, typename T>
+__device__ __forceinline__ void store_vec(float* __restrict__ p, const T (&v)[K]) {
+  float4* p4 = reinterpret_cast<float4*>(p);
+#pragma unroll
+  for (int q = 0; q < K / 4; ++q)
+    p4[q] = make_float4((float)v[4 * q + 0], (float)v[4 * q + 1], (float)v[4 * q + 2],
+                        (float)v[4 * q + 3]);
+}
+
+// ---------------------------------------------------------------------------
+// pass 1: RHS assembly + x solve.  CTA = `spc` rows, 2^log2tsys threads per
+// row, K contiguous unknowns per thread.
+// ---------------------------------------------------------------------------
+template <int K, typename T, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) x_sweep_kernel(const XArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tsys = 1 << a.log2tsys;
+  const int N = 2 * tsys;
+  Eq<T>* red = reinterpret_cast<Eq<T>*>(smem);
+  T* xs = reinterpret_cast<T*>(red + (size_t)a.spc * N);
+
+  const int tid = threadIdx.x;
+  const int sys = tid >> a.log2tsys;
+  const int p = tid & (tsys - 1);
+  const int j = blockIdx.x * a.spc + sys;
+  const int i0 = p * K;
+  const bool active = (j < a.ny) && (i0 < a.nx);
+  const size_t row = (size_t)j * a.ld;
+
+  T d[K], s[K];
+  if (active) {
+    const T cx = (T)a.cx, cy = (T)a.cy, sc = (T)a.sc;
+    float uc[K], v[K];
+    // vertical neighbours first, accumulated into d (halo rows j-1, j+1)
+    if (j > 0) {
+      load_vec<K>(v, a.u + row - a.ld + i0);
+#pragma unroll
+      for (int k = 0; k < K; ++k) d[k] = (T)v[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < K; ++k) d[k] = T(0);
+    }
+    if (j + 1 < a.ny) {
+      load_vec<K>(v, a.u + row + a.ld + i0);
+#pragma unroll
+      for (int k = 0; k < K; ++k) d[k] += (T)v[k];
+    }
+    load_vec<K>(uc, a.u + row + i0);
+    load_vec<K>(v, a.m + row + i0);
+    const float uL = (i0 > 0) ? __ldg(a.u + row + i0 - 1) : 0.f;
+    const float uR = (i0 + K < a.nx) ? __ldg(a.u + row + i0 + K) : 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const T c = (T)uc[k];
+      const T l = (T)(k > 0 ? uc[k - 1] : uL);
+      const T r = (T)(k < K - 1 ? uc[k + 1] : uR);
+      const T lap = cx * (l + r - T(2) * c) + cy * (d[k] - T(2) * c);
+      const bool ok = (i0 + k) < a.nx;
+      d[k] = ok ? (T)v[k] * lap : T(0);
+      s[k] = ok ? sc * (T)v[k] : T(0);
+    }
+    // point source f^k = w(t_k) / (h1 h2) at one node
+    const GridDev* gd = a.gd;
+    const int sx = gd->src_ix, sy = gd->src_iy;
+    if (j == sy && sx >= i0 && sx < i0 + K) {
+      const long long lev = gd->k;
+      if (gd->wavelet != nullptr && lev >= 0 && lev < gd->n_wavelet) {
+        const T f = (T)a.src_scale * (T)gd->wavelet[lev];
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          if (i0 + k == sx) d[k] += f;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < K; ++k) { d[k] = T(0); s[k] = T(0); }
+  }
+
+  Eq<T> e0, e1;
+  chunk_reduce<K, T>(d, s, e0, e1);
+  red[(size_t)sys * N + 2 * p] = e0;
+  red[(size_t)sys * N + 2 * p + 1] = e1;
+  __syncthreads();
+  reduced_solve<T>(red, xs, a.spc, N, a.log2tsys + 1, a.pcr);
+  const T x0 = xs[(size_t)sys * N + 2 * p];
+  const T xl = xs[(size_t)sys * N + 2 * p + 1];
+  chunk_backsub<K, T>(d, s, x0, xl);
+  if (active) store_vec<K, T>(a.w + row + i0, d);
+}
+
+// ---------------------------------------------------------------------------
+// pass 2: y solve + update.  A strip of 2^log2W columns; a cluster of C CTAs
+// covers the whole column length, each CTA 2^log2tcol threads per column
+// with K consecutive rows per thread.  The interface system of column c is
+// gathered into the shared memory of cluster rank (c mod C) over DSMEM,
+// solved there, and the interface values are read back the same way.
+// ---------------------------------------------------------------------------
+template <int K, typename T, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) y_sweep_kernel(const YArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int W = 1 << a.log2W;
+  const int tcol = 1 << a.log2tcol;
+  const int C = a.C;
+  const int tid = threadIdx.x;
+  const int col = tid & (W - 1);
+  const int q = tid >> a.log2W;
+  int rank = 0;
+  if (C > 1) rank = (int)cg::this_cluster().block_rank();
+  const int strip = blockIdx.x / C;
+  const int gq = rank * tcol + q;
+  const int N = 2 * C * tcol;
+  int log2N = a.log2tcol + 1;
+  for (int c = C; c > 1; c >>= 1) ++log2N;
+  const int n_slots = (W + C - 1) / C;
+  Eq<T>* red = reinterpret_cast<Eq<T>*>(smem);
+  T* xs = reinterpret_cast<T*>(red + (size_t)n_slots * N);
+  const int owner = col % C;
+  const int slot = col / C;
+
+  const int i = strip * W + col;
+  const int j0 = gq * K;
+  const bool colok = i < a.nx;
+  const T sc = (T)a.sc;
+
+  T d[K], s[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int r = j0 + k;
+    const bool ok = colok && r < a.ny;
+    const size_t idx = (size_t)r * a.ld + i;
+    d[k] = ok ? (T)__ldg(a.w + idx) : T(0);
+    s[k] = ok ? sc * (T)__ldg(a.m + idx) : T(0);
+  }
+
+  Eq<T> e0, e1;
+  chunk_reduce<K, T>(d, s, e0, e1);
+  Eq<T>* dst = red + (size_t)slot * N + 2 * gq;
+  if (C > 1) {
+    cg::cluster_group cl = cg::this_cluster();
+    dst = cl.map_shared_rank(dst, owner);
+    dst[0] = e0;
+    dst[1] = e1;
+    cl.sync();
+  } else {
+    dst[0] = e0;
+    dst[1] = e1;
+    __syncthreads();
+  }
+  const int n_own = (rank < W) ? (W - 1 - rank) / C + 1 : 0;
+  reduced_solve<T>(red, xs, n_own, N, log2N, a.pcr);
+  T x0, xl;
+  if (C > 1) {
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();
+    const T* src = cl.map_shared_rank(xs + (size_t)slot * N + 2 * gq, owner);
+    x0 = src[0];
+    xl = src[1];
+    cl.sync();  // owners keep their shared memory until every read is done
+  } else {
+    x0 = xs[(size_t)slot * N + 2 * gq];
+    xl = xs[(size_t)slot * N + 2 * gq + 1];
+  }
+  chunk_backsub<K, T>(d, s, x0, xl);
+
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int r = j0 + k;
+    if (colok && r < a.ny) {
+      const size_t idx = (size_t)r * a.ld + i;
+      const float uc = __ldg(a.u_cur + idx);
+      const float up = a.u_prev[idx];
+      const float un = 2.0f * uc - up + (float)d[k];
+      a.u_prev[idx] = un;
+      bad |= !isfinite(un);
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0 && a.err) atomicOr(a.err, ERR_NUMERIC);
+  if (blockIdx.x == 0 && tid == 0 && a.gd) a.gd->k += 1;
+}
+
+// ---------------------------------------------------------------------------
+// small kernels
+// ---------------------------------------------------------------------------
+
+// Receiver sampling after a step: traces[s][r] = u^{k}(rec r), s = k - k0 - 1.
+__global__ void gather_kernel(const GridDev* gd, const float* __restrict__ u_new, int ld) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= gd->n_rec) return;
+  const long long s = gd->k - gd->k0 - 1;
+  if (s < 0 || s >= gd->steps || gd->traces == nullptr) return;
+  const int ix = gd->rec[2 * r], iy = gd->rec[2 * r + 1];
+  gd->traces[s * gd->n_rec + r] = u_new[(size_t)iy * ld + ix];
+}
+
+// Start-up, Eq. (CN2): u^0 = phi, u^1 = phi + tau psi (+ tau^2/2 (m Lap phi + f^0)).
+__global__ void init_kernel(int nx, int ny, int ld, const float* __restrict__ m,
+                            const float* __restrict__ phi, const float* __restrict__ psi,
+                            float* __restrict__ u0, float* __restrict__ u1, double tau,
+                            double cx_half, double cy_half, int taylor, int sx, int sy,
+                            double src_half, const float* __restrict__ wavelet, int n_wavelet) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= nx || j >= ny) return;
+  const size_t c = (size_t)j * nx + i;
+  const double ph = phi[c];
+  double v = ph + (psi ? tau * (double)psi[c] : 0.0);
+  if (taylor) {
+    const double l = (i > 0) ? phi[c - 1] : 0.0;
+    const double r = (i + 1 < nx) ? phi[c + 1] : 0.0;
+    const double dn = (j > 0) ? phi[c - nx] : 0.0;
+    const double up = (j + 1 < ny) ? phi[c + nx] : 0.0;
+    const double mm = m[(size_t)j * ld + i];
+    v += mm * (cx_half * (l + r - 2.0 * ph) + cy_half * (dn + up - 2.0 * ph));
+    if (i == sx && j == sy && wavelet != nullptr && n_wavelet > 0) v += src_half * wavelet[0];
+  }
+  u0[(size_t)j * ld + i] = (float)ph;
+  u1[(size_t)j * ld + i] = (float)v;
+}
+
+// min(m), max(m) as float bit patterns (m > 0 compares as unsigned) and a
+// flag for non-finite or non-positive entries.
+__global__ void scan_m_kernel(const float* __restrict__ m, int nx, int ny, int ld,
+                              unsigned int* out3) {
+  unsigned int lo = 0x7f7fffffu, hi = 0u, bad = 0u;
+  const size_t total = (size_t)nx * ny;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const size_t j = t / nx, i = t % nx;
+    const float v = m[j * ld + i];
+    if (!(v > 0.0f) || !isfinite(v)) { bad = 1u; continue; }
+    const unsigned int b = __float_as_uint(v);
+    lo = min(lo, b);
+    hi = max(hi, b);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(out3 + 0, lo);
+    atomicMax(out3 + 1, hi);
+    atomicOr(out3 + 2, bad);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+size_t x_smem_bytes(int spc, int tsys, bool fp64) {
+  const size_t N = 2 * (size_t)tsys;
+  return fp64 ? spc * N * (sizeof(Eq<double>) + sizeof(double))
+              : spc * N * (sizeof(Eq<float>) + sizeof(float));
+}
+
+size_t y_smem_bytes(int W, int C, int tcol, bool fp64) {
+  const size_t N = 2 * (size_t)C * tcol;
+  const size_t slots = (W + C - 1) / C;
+  return fp64 ? slots * N * (sizeof(Eq<double>) + sizeof(double))
+              : slots * N * (sizeof(Eq<float>) + sizeof(float));
+}
+
+template <int K, typename T, int MAXT>
+static cudaError_t launch_x_t(const XArgs& a, cudaStream_t st) {
+  const int threads = a.spc << a.log2tsys;
+  const int blocks = (a.ny + a.spc - 1) / a.spc;
+  const size_t sm = x_smem_bytes(a.spc, 1 << a.log2tsys, sizeof(T) == 8);
+  x_sweep_kernel<K, T, MAXT><<<blocks, threads, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_x(const XArgs& a, int K, bool fp64, cudaStream_t st) {
+  if (fp64) {
+    switch (K) {
+      case 4: return launch_x_t<4, double, 512>(a, st);
+      case 8: return launch_x_t<8, double, 512>(a, st);
+      case 16: return launch_x_t<16, double, 512>(a, st);
+      case 32: return launch_x_t<32, double, 512>(a, st);
+    }
+  } else {
+    switch (K) {
+      case 4: return launch_x_t<4, float, 1024>(a, st);
+      case 8: return launch_x_t<8, float, 1024>(a, st);
+      case 16: return launch_x_t<16, float, 1024>(a, st);
+      case 32: return launch_x_t<32, float, 1024>(a, st);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int K, typename T, int MAXT>
+static cudaError_t launch_y_t(const YArgs& a, cudaStream_t st) {
+  const int W = 1 << a.log2W;
+  const int threads = W << a.log2tcol;
+  const int strips = (a.nx + W - 1) / W;
+  const size_t sm = y_smem_bytes(W, a.C, 1 << a.log2tcol, sizeof(T) == 8);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(strips * a.C, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = a.C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, y_sweep_kernel<K, T, MAXT>, a);
+}
+
+cudaError_t launch_y(const YArgs& a, int K, bool fp64, cudaStream_t st) {
+  if (fp64) {
+    switch (K) {
+      case 4: return launch_y_t<4, double, 512>(a, st);
+      case 8: return launch_y_t<8, double, 512>(a, st);
+      case 16: return launch_y_t<16, double, 512>(a, st);
+      case 32: return launch_y_t<32, double, 512>(a, st);
+    }
+  } else {
+    switch (K) {
+      case 4: return launch_y_t<4, float, 1024>(a, st);
+      case 8: return launch_y_t<8, float, 1024>(a, st);
+      case 16: return launch_y_t<16, float, 1024>(a, st);
+      case 32: return launch_y_t<32, float, 1024>(a, st);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename KernT>
+static cudaError_t allow_smem(KernT kern, bool cluster16) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024);
+  if (e != cudaSuccess) return e;
+  if (cluster16) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+
+cudaError_t configure_kernels() {
+  cudaError_t e = cudaSuccess;
+#define ADI_CFG(kern, cl)                       \
+  if (e == cudaSuccess) e = allow_smem(kern, cl);
+  ADI_CFG((x_sweep_kernel<4, float, 1024>), false)
+  ADI_CFG((x_sweep_kernel<8, float, 1024>), false)
+  ADI_CFG((x_sweep_kernel<16, float, 1024>), false)
+  ADI_CFG((x_sweep_kernel<32, float, 1024>), false)
+  ADI_CFG((x_sweep_kernel<4, double, 512>), false)
+  ADI_CFG((x_sweep_kernel<8, double, 512>), false)
+  ADI_CFG((x_sweep_kernel<16, double, 512>), false)
+  ADI_CFG((x_sweep_kernel<32, double, 512>), false)
+  ADI_CFG((y_sweep_kernel<4, float, 1024>), true)
+  ADI_CFG((y_sweep_kernel<8, float, 1024>), true)
+  ADI_CFG((y_sweep_kernel<16, float, 1024>), true)
+  ADI_CFG((y_sweep_kernel<32, float, 1024>), true)
+  ADI_CFG((y_sweep_kernel<4, double, 512>), true)
+  ADI_CFG((y_sweep_kernel<8, double, 512>), true)
+  ADI_CFG((y_sweep_kernel<16, double, 512>), true)
+  ADI_CFG((y_sweep_kernel<32, double, 512>), true)
+#undef ADI_CFG
+  return e;
+}
+
+cudaError_t launch_gather(const GridDev* gd, const float* u_new, int ld, int n_rec,
+                          cudaStream_t st) {
+  if (n_rec <= 0) return cudaSuccess;
+  const int threads = 128;
+  gather_kernel<<<(n_rec + threads - 1) / threads, threads, 0, st>>>(gd, u_new, ld);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init(int nx, int ny, int ld, const float* m_pitched, const float* phi,
+                        const float* psi, float* u0, float* u1, double tau, double cx_half,
+                        double cy_half, int taylor, int sx, int sy, double src_half,
+                        const float* wavelet, int n_wavelet, cudaStream_t st) {
+  dim3 block(256, 1, 1);
+  dim3 grid((nx + 255) / 256, ny, 1);
+  init_kernel<<<grid, block, 0, st>>>(nx, ny, ld, m_pitched, phi, psi, u0, u1, tau, cx_half,
+                                      cy_half, taylor, sx, sy, src_half, wavelet, n_wavelet);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_m(const float* m, int nx, int ny, int ld, unsigned int* out3,
+                          cudaStream_t st) {
+  scan_m_kernel<<<152 * 4, 256, 0, st>>>(m, nx, ny, ld, out3);
+  return cudaGetLastError();
+}
+
+}  // namespace adi

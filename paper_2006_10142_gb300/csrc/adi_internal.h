@@ -1,0 +1,71 @@
+// adi_internal.h -- host/device structures shared by the library's .cu files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace adi {
+
+// Per-grid state read by the kernels from device memory, so that a captured
+// CUDA graph picks up the current run's source and receivers on replay.
+struct GridDev {
+  long long k;          // time level of u_cur (u^k); the y sweep advances it
+  long long k0;         // level at the start of the current run
+  long long steps;      // length of the current run (bounds of traces)
+  const float* wavelet; // w(t_k) samples, or null
+  int n_wavelet;
+  int src_ix, src_iy;   // source node, src_ix < 0 = none
+  int n_rec;
+  const int* rec;       // [n_rec][2] receiver nodes
+  float* traces;        // [steps][n_rec]
+};
+
+// Device error word bits.
+enum : int { ERR_NUMERIC = 1, ERR_TIMEOUT = 2 };
+
+// Arguments of the fused RHS + x-sweep kernel (Eq. fr1's x operator).
+struct XArgs {
+  int nx, ny, ld;
+  int log2tsys;   // threads per row (system) = 1 << log2tsys
+  int spc;        // rows per CTA
+  int pcr;        // CR -> PCR switch size
+  const float* m;
+  const float* u;   // u^k
+  float* w;         // out: w = X^{-1} r
+  double cx, cy;    // tau^2 / h1^2, tau^2 / h2^2
+  double sc;        // tau^2 / (2 h1^2): s = sc * m
+  double src_scale; // tau^2 / (h1 h2)
+  const GridDev* gd;
+};
+
+// Arguments of the y-sweep + update kernel (Eq. fr2's y operator).
+struct YArgs {
+  int nx, ny, ld;
+  int log2W;      // columns per strip = 1 << log2W
+  int log2tcol;   // threads per column in one CTA
+  int C;          // CTAs per cluster along the column
+  int pcr;
+  const float* m;
+  const float* w;      // RHS
+  const float* u_cur;  // u^k
+  float* u_prev;       // in: u^{k-1}; out: u^{k+1}
+  double sc;           // tau^2 / (2 h2^2)
+  GridDev* gd;         // k is advanced by one CTA
+  int* err;
+};
+
+// Launchers (adi_forward.cu).
+cudaError_t launch_x(const XArgs& a, int K, bool fp64, cudaStream_t st);
+cudaError_t launch_y(const YArgs& a, int K, bool fp64, cudaStream_t st);
+cudaError_t launch_gather(const GridDev* gd, const float* u_new, int ld, int n_rec, cudaStream_t st);
+cudaError_t launch_init(int nx, int ny, int ld, const float* m_pitched, const float* phi,
+                        const float* psi, float* u0, float* u1, double tau, double cx_half,
+                        double cy_half, int taylor, int src_ix, int src_iy, double src_half,
+                        const float* wavelet, int n_wavelet, cudaStream_t st);
+cudaError_t launch_scan_m(const float* m, int nx, int ny, int ld, unsigned int* out3,
+                          cudaStream_t st);
+size_t x_smem_bytes(int spc, int tsys, bool fp64);
+size_t y_smem_bytes(int W, int C, int tcol, bool fp64);
+cudaError_t configure_kernels();
+
+}  // namespace adi

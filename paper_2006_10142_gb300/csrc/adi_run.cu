@@ -1,0 +1,462 @@
+// adi_run.cu -- handle implementation: creation, the time loop (Algorithm 1)
+// with CUDA-graph replay of step pairs, checkpoints, state access, status,
+// tuning and measurement hooks.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "adi_internal.h"
+#include "adi_run.h"
+
+using namespace adi;
+
+namespace {
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+bool g_configured = false;
+
+#define CK(call, what)                                          \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return cuda_fail(this, e_, what);    \
+  } while (0)
+
+}  // namespace
+
+int adi_wave::upload_gd(Grid& G, cudaStream_t st) {
+  CK(cudaMemcpyAsync(G.gd, &G.hgd, sizeof(GridDev), cudaMemcpyHostToDevice, st), "upload grid state");
+  return ADI_OK;
+}
+
+int adi_wave::create(const adi_wave_desc* desc, int n, const float* const* m,
+                     const float* const* phi, const float* const* psi, const adi_source* src,
+                     cudaStream_t st) {
+  if (n > 1) return fail(this, ADI_EUNSUPPORTED, "batched handles are created by adi_batch");
+  if (!g_configured) {
+    CK(configure_kernels(), "configure kernels");
+    g_configured = true;
+  }
+  CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "create capture stream");
+  CK(cudaMalloc(&d_err, sizeof(int)), "alloc error word");
+  CK(cudaMemsetAsync(d_err, 0, sizeof(int), st), "clear error word");
+  g.resize(n);
+  for (int s = 0; s < n; ++s) {
+    Grid& G = g[s];
+    const adi_wave_desc& d = desc[s];
+    G.nx = d.nx;
+    G.ny = d.ny;
+    G.ld = round_up(d.nx, 32);
+    G.lx = d.lx;
+    G.ly = d.ly;
+    G.dt = d.dt;
+    G.hx = d.lx / (d.nx + 1);
+    G.hy = d.ly / (d.ny + 1);
+    G.start = d.start;
+    G.fp64mode = d.fp64_solve;
+    const size_t bytes = sizeof(float) * (size_t)G.ld * G.ny;
+    cudaError_t e = cudaMalloc(&G.m, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&G.buf[0], bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&G.buf[1], bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&G.w, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&G.gd, sizeof(GridDev));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(this, e == cudaErrorMemoryAllocation ? ADI_ENOMEM : ADI_ECUDA,
+                  std::string("allocate grid: ") + cudaGetErrorString(e));
+    }
+    CK(cudaMemsetAsync(G.m, 0, bytes, st), "clear m");
+    CK(cudaMemsetAsync(G.buf[0], 0, bytes, st), "clear u0");
+    CK(cudaMemsetAsync(G.buf[1], 0, bytes, st), "clear u1");
+    CK(cudaMemsetAsync(G.w, 0, bytes, st), "clear w");
+    int rc = start_grid(s, m[s], phi[s], psi ? psi[s] : nullptr, src ? &src[s] : nullptr, st);
+    if (rc != ADI_OK) return rc;
+  }
+  return ADI_OK;
+}
+
+// Copy m (optional), re-plan, and run the start-up of Eq. (CN2) for shot s.
+int adi_wave::start_grid(int s, const float* m, const float* phi, const float* psi,
+                         const adi_source* sr, cudaStream_t st) {
+  Grid& G = g[s];
+  if (m) {
+    CK(cudaMemcpy2DAsync(G.m, sizeof(float) * G.ld, m, sizeof(float) * G.nx,
+                         sizeof(float) * G.nx, G.ny, cudaMemcpyDeviceToDevice, st), "copy m");
+    if (!scan) CK(cudaMalloc(&scan, 3 * sizeof(unsigned int)), "alloc scan");
+    const unsigned int init3[3] = {0x7f7fffffu, 0u, 0u};
+    unsigned int res3[3];
+    CK(cudaMemcpyAsync(scan, init3, sizeof(init3), cudaMemcpyHostToDevice, st), "scan init");
+    CK(launch_scan_m(G.m, G.nx, G.ny, G.ld, scan, st), "scan m");
+    CK(cudaMemcpyAsync(res3, scan, sizeof(res3), cudaMemcpyDeviceToHost, st), "scan read");
+    CK(cudaStreamSynchronize(st), "scan sync");
+    launches += 1;
+    if (res3[2]) return fail(this, ADI_EINVAL, "m must be finite and > 0 everywhere");
+    float lo, hi;
+    memcpy(&lo, &res3[0], 4);
+    memcpy(&hi, &res3[1], 4);
+    G.mmin = lo;
+    G.mmax = hi;
+    std::string why;
+    GridPlan old = G.plan;
+    int rc = plan_grid(G, tuning, why);
+    if (rc != ADI_OK) {
+      G.plan = old;
+      return fail(this, rc, why);
+    }
+    drop_graphs();
+  }
+  G.hgd = GridDev{};
+  G.hgd.k = 1;
+  G.hgd.k0 = 1;
+  G.hgd.src_ix = -1;
+  G.hgd.src_iy = -1;
+  if (upload_gd(G, st) != ADI_OK) return ADI_ECUDA;
+  const bool has_src = sr && sr->ix >= 0 && sr->wavelet && sr->n_wavelet > 0;
+  CK(launch_init(G.nx, G.ny, G.ld, G.m, phi, psi, G.buf[0], G.buf[1], G.dt,
+                 G.dt * G.dt / (2.0 * G.hx * G.hx), G.dt * G.dt / (2.0 * G.hy * G.hy),
+                 G.start == ADI_START_TAYLOR2 ? 1 : 0, has_src ? sr->ix : -1,
+                 has_src ? sr->iy : -1, G.dt * G.dt / (2.0 * G.hx * G.hy),
+                 has_src ? sr->wavelet : nullptr, has_src ? sr->n_wavelet : 0, st),
+     "init kernel");
+  launches += 1;
+  G.cur = 1;
+  G.k = 1;
+  rr.valid = false;
+  return ADI_OK;
+}
+
+int adi_wave::reset(const float* const* m, const float* const* phi, const float* const* psi,
+                    const adi_source* src, cudaStream_t st) {
+  for (size_t s = 0; s < g.size(); ++s) {
+    if (!phi[s]) return fail(this, ADI_EINVAL, "phi is required");
+    if (src && src[s].ix >= 0 &&
+        (src[s].ix >= g[s].nx || src[s].iy < 0 || src[s].iy >= g[s].ny))
+      return fail(this, ADI_EINVAL, "source node outside the grid");
+  }
+  for (size_t s = 0; s < g.size(); ++s) {
+    int rc = start_grid((int)s, m ? m[s] : nullptr, phi[s], psi ? psi[s] : nullptr,
+                        src ? &src[s] : nullptr, st);
+    if (rc != ADI_OK) return rc;
+  }
+  return ADI_OK;
+}
+
+int adi_wave::prof_begin(cudaStream_t st, cudaEvent_t* a) {
+  if (ev_pool.empty()) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e), "event create");
+    ev_pool.push_back(e);
+  }
+  *a = ev_pool.back();
+  ev_pool.pop_back();
+  CK(cudaEventRecord(*a, st), "event record");
+  return ADI_OK;
+}
+
+int adi_wave::prof_end(cudaStream_t st, cudaEvent_t a, int kind) {
+  if (ev_pool.empty()) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e), "event create");
+    ev_pool.push_back(e);
+  }
+  cudaEvent_t b = ev_pool.back();
+  ev_pool.pop_back();
+  CK(cudaEventRecord(b, st), "event record");
+  prof.push_back(ProfRec{a, b, kind});
+  return ADI_OK;
+}
+
+int adi_wave::enqueue_step(Grid& G, cudaStream_t st, bool gather) {
+  const GridPlan& P = G.plan;
+  float* u_cur = G.buf[G.cur];
+  float* u_prev = G.buf[1 - G.cur];
+  XArgs xa;
+  xa.nx = G.nx;
+  xa.ny = G.ny;
+  xa.ld = G.ld;
+  xa.log2tsys = P.log2tsys;
+  xa.spc = P.spc;
+  xa.pcr = P.pcr;
+  xa.m = G.m;
+  xa.u = u_cur;
+  xa.w = G.w;
+  xa.cx = G.dt * G.dt / (G.hx * G.hx);
+  xa.cy = G.dt * G.dt / (G.hy * G.hy);
+  xa.sc = G.dt * G.dt / (2.0 * G.hx * G.hx);
+  xa.src_scale = G.dt * G.dt / (G.hx * G.hy);
+  xa.gd = G.gd;
+  YArgs ya;
+  ya.nx = G.nx;
+  ya.ny = G.ny;
+  ya.ld = G.ld;
+  ya.log2W = P.log2W;
+  ya.log2tcol = P.log2tcol;
+  ya.C = P.C;
+  ya.pcr = P.pcr;
+  ya.m = G.m;
+  ya.w = G.w;
+  ya.u_cur = u_cur;
+  ya.u_prev = u_prev;
+  ya.sc = G.dt * G.dt / (2.0 * G.hy * G.hy);
+  ya.gd = G.gd;
+  ya.err = d_err;
+
+  cudaEvent_t a = nullptr;
+  if (profile && prof_begin(st, &a) != ADI_OK) return ADI_ECUDA;
+  CK(launch_x(xa, P.kx, P.fp64x, st), "x sweep launch");
+  if (profile && prof_end(st, a, ADI_KERNEL_X) != ADI_OK) return ADI_ECUDA;
+  if (profile && prof_begin(st, &a) != ADI_OK) return ADI_ECUDA;
+  CK(launch_y(ya, P.ky, P.fp64y, st), "y sweep launch");
+  if (profile && prof_end(st, a, ADI_KERNEL_Y) != ADI_OK) return ADI_ECUDA;
+  launches += 2;
+  if (gather) {
+    CK(launch_gather(G.gd, u_prev, G.ld, G.hgd.n_rec, st), "gather launch");
+    launches += 1;
+  }
+  G.cur = 1 - G.cur;
+  G.k += 1;
+  return ADI_OK;
+}
+
+void adi_wave::drop_graphs() {
+  for (int o = 0; o < 2; ++o)
+    for (int q = 0; q < 2; ++q)
+      if (pair[o][q]) {
+        cudaGraphExecDestroy(pair[o][q]);
+        pair[o][q] = nullptr;
+      }
+}
+
+int adi_wave::launch_pair_graph(Grid& G, cudaStream_t st, bool gather) {
+  cudaGraphExec_t& ex = pair[G.cur][gather ? 1 : 0];
+  if (!ex) {
+    const int cur0 = G.cur;
+    const long long k0 = G.k;
+    const int64_t l0 = launches;
+    CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    int rc = enqueue_step(G, cap, gather);
+    if (rc == ADI_OK) rc = enqueue_step(G, cap, gather);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cap, &graph);
+    G.cur = cur0;
+    G.k = k0;
+    launches = l0;
+    if (rc != ADI_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(this, e, "end capture");
+    e = cudaGraphInstantiate(&ex, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      ex = nullptr;
+      return cuda_fail(this, e, "graph instantiate");
+    }
+  }
+  CK(cudaGraphLaunch(ex, st), "graph launch");
+  launches += gather ? 6 : 4;
+  G.k += 2;
+  return ADI_OK;
+}
+
+int adi_wave::run(int steps, const adi_source* src, const int32_t* rec_xy, int n_rec,
+                  float* traces, cudaStream_t st, bool record) {
+  if (steps < 0 || n_rec < 0) return fail(this, ADI_EINVAL, "negative steps or receiver count");
+  if (n_rec > 0 && (g.size() != 1 || !rec_xy || !traces))
+    return fail(this, ADI_EINVAL, "receivers need one grid, rec_xy and traces");
+  for (size_t s = 0; s < g.size(); ++s) {
+    if (src && src[s].ix >= 0 &&
+        (src[s].ix >= g[s].nx || src[s].iy < 0 || src[s].iy >= g[s].ny))
+      return fail(this, ADI_EINVAL, "source node outside the grid");
+  }
+  if (g.size() != 1) return fail(this, ADI_EUNSUPPORTED, "batched run");
+  Grid& G = g[0];
+  for (int r = 0; r < n_rec; ++r) {
+    if (rec_xy[2 * r] < 0 || rec_xy[2 * r] >= G.nx || rec_xy[2 * r + 1] < 0 ||
+        rec_xy[2 * r + 1] >= G.ny)
+      return fail(this, ADI_EINVAL, "receiver node outside the grid");
+  }
+  if (steps == 0) return ADI_OK;
+
+  // per-run device state: level, source, receivers
+  if (n_rec > rec_cap) {
+    if (d_rec) cudaFree(d_rec);
+    d_rec = nullptr;
+    rec_cap = 0;
+    CK(cudaMalloc(&d_rec, sizeof(int) * 2 * (size_t)n_rec), "alloc receivers");
+    rec_cap = n_rec;
+  }
+  if (n_rec > 0)
+    CK(cudaMemcpyAsync(d_rec, rec_xy, sizeof(int) * 2 * (size_t)n_rec, cudaMemcpyHostToDevice, st),
+       "copy receivers");
+  const adi_source none = {-1, -1, nullptr, 0};
+  const adi_source sr = src ? src[0] : none;
+  G.hgd.k = G.k;
+  G.hgd.k0 = G.k;
+  G.hgd.steps = steps;
+  G.hgd.wavelet = (sr.ix >= 0) ? sr.wavelet : nullptr;
+  G.hgd.n_wavelet = (sr.ix >= 0 && sr.wavelet) ? sr.n_wavelet : 0;
+  G.hgd.src_ix = (sr.ix >= 0 && sr.wavelet) ? sr.ix : -1;
+  G.hgd.src_iy = (sr.ix >= 0 && sr.wavelet) ? sr.iy : -1;
+  G.hgd.n_rec = n_rec;
+  G.hgd.rec = d_rec;
+  G.hgd.traces = traces;
+  if (upload_gd(G, st) != ADI_OK) return ADI_ECUDA;
+
+  const int every = record ? ckpt_every : 0;
+  if (record) {
+    rr.valid = true;
+    rr.k0 = G.k;
+    rr.steps = steps;
+    rr.every = every;
+    rr.src = sr;
+    rr.rec.assign(rec_xy ? rec_xy : (const int32_t*)nullptr,
+                  rec_xy ? rec_xy + 2 * (size_t)n_rec : (const int32_t*)nullptr);
+    const size_t need = every > 0 ? (size_t)((steps + every - 1) / every) : 0;
+    const size_t fbytes = sizeof(float) * (size_t)G.ld * G.ny;
+    if (rr.ckpt_bytes != fbytes) {
+      for (float* p : rr.ckpt) cudaFree(p);
+      rr.ckpt.clear();
+      rr.ckpt_bytes = fbytes;
+    }
+    while (rr.ckpt.size() < need) {
+      float* p = nullptr;
+      cudaError_t e = cudaMalloc(&p, 2 * fbytes);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        rr.valid = false;
+        return fail(this, ADI_ENOMEM, "allocate checkpoints");
+      }
+      rr.ckpt.push_back(p);
+    }
+  }
+
+  const bool gather = n_rec > 0;
+  const bool use_graph = G.plan.graph && !profile;
+  const size_t fbytes = sizeof(float) * (size_t)G.ld * G.ny;
+  int s = 0;
+  while (s < steps) {
+    int seg = steps - s;
+    if (every > 0) {
+      if (s % every == 0) {
+        float* c = rr.ckpt[s / every];
+        CK(cudaMemcpyAsync(c, G.buf[1 - G.cur], fbytes, cudaMemcpyDeviceToDevice, st), "checkpoint");
+        CK(cudaMemcpyAsync(c + (size_t)G.ld * G.ny, G.buf[G.cur], fbytes, cudaMemcpyDeviceToDevice,
+                           st), "checkpoint");
+      }
+      seg = std::min(seg, every - s % every);
+    }
+    int t = 0;
+    if (use_graph) {
+      while (seg - t >= 2) {
+        int rc = launch_pair_graph(G, st, gather);
+        if (rc != ADI_OK) return rc;
+        t += 2;
+      }
+    }
+    while (t < seg) {
+      int rc = enqueue_step(G, st, gather);
+      if (rc != ADI_OK) return rc;
+      t += 1;
+    }
+    s += seg;
+  }
+  G.hgd.k = G.k;
+  return ADI_OK;
+}
+
+int adi_wave::set_state(int shot, const float* u_prev, const float* u_cur, int64_t k,
+                        cudaStream_t st) {
+  Grid& G = g[shot];
+  const size_t wb = sizeof(float) * (size_t)G.nx;
+  CK(cudaMemcpy2DAsync(G.buf[1 - G.cur], sizeof(float) * G.ld, u_prev, wb, wb, G.ny,
+                       cudaMemcpyDeviceToDevice, st), "set_state");
+  CK(cudaMemcpy2DAsync(G.buf[G.cur], sizeof(float) * G.ld, u_cur, wb, wb, G.ny,
+                       cudaMemcpyDeviceToDevice, st), "set_state");
+  G.k = k;
+  G.hgd.k = k;
+  G.hgd.k0 = k;
+  G.hgd.steps = 0;
+  if (upload_gd(G, st) != ADI_OK) return ADI_ECUDA;
+  rr.valid = false;
+  return ADI_OK;
+}
+
+int adi_wave::sync_status(cudaStream_t st) {
+  CK(cudaStreamSynchronize(st), "synchronize");
+  int word = 0;
+  CK(cudaMemcpy(&word, d_err, sizeof(int), cudaMemcpyDeviceToHost), "read error word");
+  CK(cudaMemset(d_err, 0, sizeof(int)), "clear error word");
+  if (word & ERR_TIMEOUT) return fail(this, ADI_ETIMEOUT, "a bounded device wait expired");
+  if (word & ERR_NUMERIC) return fail(this, ADI_ENUMERIC, "non-finite value in the wavefield");
+  return ADI_OK;
+}
+
+int adi_wave::set_tuning(const adi_wave_tuning& t) {
+  std::vector<GridPlan> old;
+  for (auto& G : g) old.push_back(G.plan);
+  for (auto& G : g) {
+    std::string why;
+    int rc = plan_grid(G, t, why);
+    if (rc != ADI_OK) {
+      for (size_t s = 0; s < g.size(); ++s) g[s].plan = old[s];
+      return fail(this, rc, why);
+    }
+  }
+  tuning = t;
+  drop_graphs();
+  return ADI_OK;
+}
+
+int adi_wave::profile_read(double* ms, int64_t* counts, int n_kinds) {
+  std::vector<double> acc(ADI_KERNEL_KINDS, 0.0);
+  std::vector<int64_t> cnt(ADI_KERNEL_KINDS, 0);
+  for (const ProfRec& r : prof) {
+    CK(cudaEventSynchronize(r.b), "event sync");
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, r.a, r.b), "event elapsed");
+    acc[r.kind] += t;
+    cnt[r.kind] += 1;
+    ev_pool.push_back(r.a);
+    ev_pool.push_back(r.b);
+  }
+  prof.clear();
+  for (int k = 0; k < n_kinds && k < ADI_KERNEL_KINDS; ++k) {
+    if (ms) ms[k] = acc[k];
+    if (counts) counts[k] = cnt[k];
+  }
+  return ADI_OK;
+}
+
+adi_wave::~adi_wave() {
+  cudaDeviceSynchronize();
+  drop_graphs();
+  for (auto& G : g) {
+    cudaFree(G.m);
+    cudaFree(G.buf[0]);
+    cudaFree(G.buf[1]);
+    cudaFree(G.w);
+    cudaFree(G.gd);
+  }
+  for (float* p : rr.ckpt) cudaFree(p);
+  for (const ProfRec& r : prof) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+  if (d_err) cudaFree(d_err);
+  if (scan) cudaFree(scan);
+  if (d_rec) cudaFree(d_rec);
+  if (cap) cudaStreamDestroy(cap);
+}
+
+int adi_wave::adjoint(const float* resid, double* grad_m, float* grad_wavelet, int every,
+                      cudaStream_t st) {
+  (void)resid; (void)grad_m; (void)grad_wavelet; (void)every; (void)st;
+  return fail(this, ADI_EUNSUPPORTED, "adjoint not built yet");
+}

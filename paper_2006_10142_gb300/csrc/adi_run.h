@@ -1,0 +1,107 @@
+// adi_run.h -- the handle behind the C ABI (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/adiwave.h"
+#include "adi_internal.h"
+
+namespace adi {
+
+// Diagonal dominance ratio above which the elimination runs in FP64.
+constexpr double kWeakDominance = 0.9;
+
+struct GridPlan {
+  // x sweep
+  int kx = 16, log2tsys = 0, spc = 1, pcr = 32;
+  bool fp64x = false;
+  // y sweep
+  int ky = 8, log2W = 3, log2tcol = 0, C = 1;
+  bool fp64y = false;
+  int graph = 1;
+};
+
+struct Grid {
+  int nx = 0, ny = 0, ld = 0;
+  double lx = 1, ly = 1, dt = 0, hx = 0, hy = 0;
+  int start = 0, fp64mode = 0;
+  float* m = nullptr;               // [ny][ld]
+  float* buf[2] = {nullptr, nullptr};  // buf[cur] = u^k, buf[1-cur] = u^{k-1}
+  float* w = nullptr;               // scratch [ny][ld]
+  int cur = 1;
+  long long k = 1;
+  GridDev* gd = nullptr;            // device copy
+  GridDev hgd = {};                 // host mirror
+  double mmin = 0, mmax = 0;
+  GridPlan plan;
+};
+
+// What adi_wave_adjoint needs to replay the last run.
+struct RunRecord {
+  bool valid = false;
+  long long k0 = 0;
+  int steps = 0;
+  int every = 0;
+  adi_source src = {-1, -1, nullptr, 0};
+  std::vector<int> rec;             // [n_rec][2] host copy
+  std::vector<float*> ckpt;         // checkpoint c: 2 fields (u^{k-1}, u^k) at step c*every
+  size_t ckpt_bytes = 0;
+};
+
+struct ProfRec {
+  cudaEvent_t a, b;
+  int kind;
+};
+
+}  // namespace adi
+
+struct adi_wave {
+  std::vector<adi::Grid> g;
+  int* d_err = nullptr;
+  int* d_rec = nullptr;
+  unsigned int* scan = nullptr;
+  int rec_cap = 0;
+  cudaStream_t cap = nullptr;  // private stream used only for graph capture
+  cudaGraphExec_t pair[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [orientation][gather]
+  adi_wave_tuning tuning = {0, 0, 0, 0, 0, 0};
+  int ckpt_every = 0;
+  adi::RunRecord rr;
+  bool profile = false;
+  std::vector<adi::ProfRec> prof;
+  std::vector<cudaEvent_t> ev_pool;
+  int64_t launches = 0;
+  std::string err;
+
+  int create(const adi_wave_desc* desc, int n, const float* const* m, const float* const* phi,
+             const float* const* psi, const adi_source* src, cudaStream_t st);
+  int reset(const float* const* m, const float* const* phi, const float* const* psi,
+            const adi_source* src, cudaStream_t st);
+  int start_grid(int s, const float* m, const float* phi, const float* psi, const adi_source* sr,
+                 cudaStream_t st);
+  int run(int steps, const adi_source* src, const int32_t* rec_xy, int n_rec, float* traces,
+          cudaStream_t st, bool record);
+  int adjoint(const float* resid, double* grad_m, float* grad_wavelet, int every, cudaStream_t st);
+  int set_state(int shot, const float* u_prev, const float* u_cur, int64_t k, cudaStream_t st);
+  int sync_status(cudaStream_t st);
+  int set_tuning(const adi_wave_tuning& t);
+  int profile_read(double* ms, int64_t* launches, int n_kinds);
+  ~adi_wave();
+
+  // internals
+  int enqueue_step(adi::Grid& G, cudaStream_t st, bool gather);
+  int launch_pair_graph(adi::Grid& G, cudaStream_t st, bool gather);
+  void drop_graphs();
+  int prof_begin(cudaStream_t st, cudaEvent_t* a);
+  int prof_end(cudaStream_t st, cudaEvent_t a, int kind);
+  int upload_gd(adi::Grid& G, cudaStream_t st);
+};
+
+namespace adi {
+int fail(adi_wave* h, int code, const std::string& msg);
+int cuda_fail(adi_wave* h, cudaError_t e, const char* what);
+int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why);
+}  // namespace adi

@@ -1,0 +1,189 @@
+"""GPU parity of the forward ADI path (C ABI) against the FP64 oracle.
+
+Bar: relative L2 <= 1e-4 per field after the run (FP32 GPU vs FP64 oracle on
+the same FP32-rounded inputs).  Grids cover one and several tiles per line,
+ragged tails (sizes that are not multiples of the chunk, the strip width or
+a power of two), degenerate 1-wide grids, non-square grids, every chunk
+length and CR-to-PCR switch size, the cluster path of the y sweep, the FP64
+fallback, the Taylor start, receivers and graph replay.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2006_10142_gb300 import inputs
+from helpers import gpu_run, oracle_run, rel_l2, smooth_state
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+def _problem(nx, ny, steps, seed=0, cfl=0.5, with_src=True):
+    m = inputs.m_field(nx, ny, seed)
+    h = min(1.0 / (nx + 1), 1.0 / (ny + 1))
+    tau = cfl * h / math.sqrt(m.max())
+    phi = smooth_state(nx, ny, seed, 1e-2)
+    src = (nx // 3, (2 * ny) // 3) if with_src else None
+    wav = inputs.wavelet_samples(steps + 2, tau, fp=3.0) if with_src else None
+    return m, phi, tau, src, wav
+
+
+def test_standing_wave_128_closed_form():
+    prob = inputs.standing_wave_problem(128, 200)
+    g = gpu_run(prob.m, prob.phi, prob.tau, prob.steps)
+    o = oracle_run(prob.m, prob.phi, prob.tau, prob.steps)
+    assert g["k"] == 201
+    e_prev = rel_l2(g["u_prev"], o["u_prev"])
+    e_cur = rel_l2(g["u_cur"], o["u_cur"])
+    assert e_prev < TOL and e_cur < TOL, (e_prev, e_cur)
+    # exact discrete solution of the (1,1) mode: v^K = cos((K - 1/2) th) / cos(th / 2)
+    n, tau = 128, prob.tau
+    h = 1.0 / (n + 1)
+    P = 4.0 / h ** 2 * math.sin(math.pi * h / 2) ** 2
+    s = tau * tau / 2
+    th = math.acos(1 - tau * tau * 2 * P / (2 * (1 + s * P) ** 2))
+    K = 201
+    amp = math.cos((K - 0.5) * th) / math.cos(th / 2)
+    assert rel_l2(g["u_cur"], amp * prob.phi) < TOL
+
+
+@pytest.mark.parametrize("nx,ny", [(37, 53), (1, 17), (17, 1), (1, 1), (100, 3), (129, 257),
+                                   (300, 40), (513, 200), (1000, 700)])
+def test_ragged_grids_match_oracle(nx, ny):
+    steps = 12
+    m, phi, tau, src, wav = _problem(nx, ny, steps, seed=nx + ny)
+    rec = np.array([[i % nx, (3 * i) % ny] for i in range(5)], dtype=np.int32)
+    g = gpu_run(m, phi, tau, steps, src=src, wavelet=wav, rec=rec)
+    o = oracle_run(m, phi, tau, steps, src=src, wavelet=wav, rec=rec)
+    assert rel_l2(g["u_cur"], o["u_cur"]) < TOL
+    assert rel_l2(g["u_prev"], o["u_prev"]) < TOL
+    assert rel_l2(g["traces"], o["traces"]) < TOL
+
+
+@pytest.mark.parametrize("kx,ky,pcr,W", [(4, 4, 32, 8), (8, 8, 2, 16), (16, 16, 8, 32),
+                                         (32, 32, 32, 8), (16, 4, 16, 4), (4, 32, 4, 32)])
+def test_tuning_variants_match_oracle(kx, ky, pcr, W):
+    nx, ny, steps = 300, 260, 8
+    m, phi, tau, src, wav = _problem(nx, ny, steps, seed=7)
+    tun = dict(chunk_x=kx, chunk_y=ky, pcr_size=pcr, cols_per_cta=W)
+    g = gpu_run(m, phi, tau, steps, src=src, wavelet=wav, tuning=tun)
+    o = oracle_run(m, phi, tau, steps, src=src, wavelet=wav)
+    assert g["tuning"]["chunk_x"] == kx and g["tuning"]["chunk_y"] == ky
+    assert rel_l2(g["u_cur"], o["u_cur"]) < TOL
+
+
+@pytest.mark.parametrize("ny,ky", [(4096, 4), (8191, 4), (3000, 8)])
+def test_cluster_y_sweep_matches_oracle(ny, ky):
+    """Columns long enough that the y sweep spans a thread-block cluster (DSMEM)."""
+    nx, steps = 40, 6
+    m, phi, tau, src, wav = _problem(nx, ny, steps, seed=3)
+    g = gpu_run(m, phi, tau, steps, src=src, wavelet=wav, tuning=dict(chunk_y=ky))
+    o = oracle_run(m, phi, tau, steps, src=src, wavelet=wav)
+    assert rel_l2(g["u_cur"], o["u_cur"]) < TOL
+
+
+def test_long_rows_single_cta():
+    nx, ny, steps = 16384, 24, 4
+    m, phi, tau, src, wav = _problem(nx, ny, steps, seed=4)
+    g = gpu_run(m, phi, tau, steps, src=src, wavelet=wav)
+    o = oracle_run(m, phi, tau, steps, src=src, wavelet=wav)
+    assert rel_l2(g["u_cur"], o["u_cur"]) < TOL
+
+
+def test_graph_replay_equals_direct_launches():
+    nx, ny, steps = 200, 180, 10
+    m, phi, tau, src, wav = _problem(nx, ny, steps, seed=11)
+    a = gpu_run(m, phi, tau, steps, src=src, wavelet=wav, tuning=dict(use_graph=1))
+    b = gpu_run(m, phi, tau, steps, src=src, wavelet=wav, tuning=dict(use_graph=-1))
+    np.testing.assert_array_equal(a["u_cur"], b["u_cur"])
+    np.testing.assert_array_equal(a["u_prev"], b["u_prev"])
+
+
+def test_taylor_start_and_velocity():
+    nx, ny, steps = 64, 48, 30
+    m, phi, tau, src, wav = _problem(nx, ny, steps, seed=2)
+    psi = smooth_state(nx, ny, 9, 1e-2)
+    g = gpu_run(m, phi, tau, steps, psi=psi, src=src, wavelet=wav, start="taylor2")
+    o = oracle_run(m, phi, tau, steps, psi=psi, src=src, wavelet=wav, start="taylor2")
+    assert rel_l2(g["u_cur"], o["u_cur"]) < TOL
+
+
+def test_non_unit_domain():
+    nx, ny, steps = 90, 70, 15
+    m, phi, tau, src, wav = _problem(nx, ny, steps, seed=5)
+    g = gpu_run(m, phi, tau * 2, steps, src=src, wavelet=wav, lx=2.0, ly=1.5)
+    o = oracle_run(m, phi, tau * 2, steps, src=src, wavelet=wav, lx=2.0, ly=1.5)
+    assert rel_l2(g["u_cur"], o["u_cur"]) < TOL
+
+
+@pytest.mark.parametrize("fp64", ["auto", "always"])
+def test_fp64_fallback_weak_dominance(fp64):
+    """tau = 5h: (|a| + |c|)/|b| = 2s/(1 + 2s) > 0.9, the FP64 elimination path."""
+    nx, ny, steps = 120, 90, 10
+    h = 1.0 / (nx + 1)
+    m = np.ones((ny, nx))
+    phi = smooth_state(nx, ny, 1)
+    tau = 5 * h
+    g = gpu_run(m, phi, tau, steps, fp64=fp64)
+    o = oracle_run(m, phi, tau, steps)
+    assert rel_l2(g["u_cur"], o["u_cur"]) < TOL
+
+
+def test_state_roundtrip_and_levels():
+    import torch
+    from paper_2006_10142_gb300 import api
+    nx, ny = 50, 40
+    m, phi, tau, src, wav = _problem(nx, ny, 5, seed=1)
+    dev = torch.device("cuda:0")
+    h = api.AdiWave(torch.tensor(m, dtype=torch.float32, device=dev),
+                    torch.tensor(phi, dtype=torch.float32, device=dev), tau)
+    up, uc, k = h.state()
+    assert k == 1
+    np.testing.assert_array_equal(up.cpu().numpy(), phi.astype(np.float32))
+    h.run(3)
+    _, _, k = h.state()
+    assert k == 4
+    a = torch.randn(ny, nx, device=dev)
+    b = torch.randn(ny, nx, device=dev)
+    h.set_state(a, b, 17)
+    up, uc, k = h.state()
+    assert k == 17 and torch.equal(up, a) and torch.equal(uc, b)
+    h.step()
+    _, _, k = h.state()
+    assert k == 18
+    h.close()
+
+
+def test_non_finite_state_sets_numeric_flag():
+    import torch
+    from paper_2006_10142_gb300 import api
+    nx, ny = 33, 21
+    dev = torch.device("cuda:0")
+    h = api.AdiWave(torch.ones(ny, nx, device=dev), torch.zeros(ny, nx, device=dev), 0.01)
+    bad = torch.zeros(ny, nx, device=dev)
+    bad[3, 4] = float("nan")
+    h.set_state(bad, bad, 1)
+    h.step()
+    with pytest.raises(api.AdiError) as ei:
+        h.sync_status()
+    assert ei.value.code == 4
+    h.sync_status()  # the word was cleared
+    h.close()
+
+
+def test_invalid_run_arguments():
+    import torch
+    from paper_2006_10142_gb300 import api
+    dev = torch.device("cuda:0")
+    h = api.AdiWave(torch.ones(10, 12, device=dev), torch.zeros(10, 12, device=dev), 0.01)
+    with pytest.raises(api.AdiError):
+        h.run(3, src=(12, 0), wavelet=torch.zeros(5, device=dev))
+    with pytest.raises(api.AdiError):
+        h.run(3, rec=[[0, 10]])
+    with pytest.raises(api.AdiError):
+        h.set_tuning(chunk_x=5)
+    h.close()
+    with pytest.raises(api.AdiError):
+        api.AdiWave(-torch.ones(10, 12, device=dev), torch.zeros(10, 12, device=dev), 0.01)

@@ -1,0 +1,82 @@
+"""Parity at the full workload sizes (4096^2 x 1000 steps, 16384^2 x 200
+steps), in the launch configuration the benchmark uses.
+
+A whole FP64 run at these sizes is too slow for a test, so the checks are:
+  - the first steps of the run against the oracle's run from the same start;
+  - one step from the GPU's own final state (u^{k-1}, u^k), recomputed by the
+    oracle in FP64, against the GPU's next step (the step map itself);
+  - sanity of the long run (finite, non-trivial, source energy arrived).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2006_10142_gb300 import inputs
+from helpers import THREADS, f32, rel_l2
+
+import oracle
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+def _gpu_handle(prob):
+    import torch
+    from paper_2006_10142_gb300 import api
+    dev = torch.device("cuda:0")
+    m = torch.from_numpy(f32(prob.m)).to(dev)
+    phi = torch.zeros_like(m)
+    wav = torch.from_numpy(f32(prob.wavelet)).to(dev)
+    h = api.AdiWave(m, phi, prob.tau, src=prob.src, wavelet=wav)
+    return h, wav
+
+
+def _one_step_parity(h, prob, wav):
+    up, uc, k = h.state()
+    h.step(src=prob.src, wavelet=wav)
+    _, un, k2 = h.state()
+    assert k2 == k + 1
+    n = prob.n
+    hx = 1.0 / (n + 1)
+    wv = float(f32(prob.wavelet)[k]) if k < len(prob.wavelet) else 0.0
+    ref = oracle.adi_step(f32(prob.m).astype(np.float64), up.double().cpu().numpy(),
+                          uc.double().cpu().numpy(), hx, hx, prob.tau, wv=wv, src=prob.src,
+                          threads=THREADS)
+    got = un.double().cpu().numpy()
+    # the increment z = u^{k+1} - 2u^k + u^{k-1} is what the step computes
+    z_ref = ref - 2 * uc.double().cpu().numpy() + up.double().cpu().numpy()
+    z_got = got - 2 * uc.double().cpu().numpy() + up.double().cpu().numpy()
+    return rel_l2(got, ref), rel_l2(z_got, z_ref)
+
+
+def test_ricker_4096_1000_steps():
+    prob = inputs.ricker_problem(4096, 1000, seed=0, m_dtype=np.float32)
+    h, wav = _gpu_handle(prob)
+    # first 60 steps against the oracle's run
+    h.run(60, src=prob.src, wavelet=wav)
+    _, uc, _ = h.state()
+    m64 = f32(prob.m).astype(np.float64)
+    hx = 1.0 / 4097
+    z = np.zeros((4096, 4096))
+    _, ref, _ = oracle.adi_run(m64, z, z, hx, hx, prob.tau, 60, k0=1, src=prob.src,
+                               wavelet=f32(prob.wavelet).astype(np.float64), threads=THREADS)
+    assert rel_l2(uc.double().cpu().numpy(), ref) < 1e-4
+    # the rest of the run, then one step checked against the oracle's step map
+    h.run(1000 - 60, src=prob.src, wavelet=wav)
+    h.sync_status()
+    e_u, e_z = _one_step_parity(h, prob, wav)
+    assert e_u < 1e-5 and e_z < 1e-4, (e_u, e_z)
+    _, uc, k = h.state()
+    assert k == 1002
+    assert float(uc.abs().max()) > 0
+    h.close()
+
+
+def test_ricker_16384_200_steps():
+    prob = inputs.ricker_problem(16384, 200, seed=0, m_dtype=np.float32)
+    h, wav = _gpu_handle(prob)
+    h.run(200, src=prob.src, wavelet=wav)
+    h.sync_status()
+    e_u, e_z = _one_step_parity(h, prob, wav)
+    assert e_u < 1e-5 and e_z < 1e-4, (e_u, e_z)
+    h.close()
