@@ -73,7 +73,11 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
     if (spc == 0) spc = std::max(1, std::min(maxT / tsys, G.ny / 304));
     if (spc < 1 || spc * tsys > maxT) { why = "rows_per_cta too large"; return ADI_EINVAL; }
     // whole warps only: the interface solve uses full-warp shuffles
-    if (spc * tsys < 32) spc = 32 / tsys;
+    if (tsys < 32) {
+      const int q = 32 / tsys;
+      spc = (spc + q - 1) / q * q;
+      if (spc * tsys > maxT) spc = maxT / tsys;
+    }
     int pcr = t.pcr_size ? t.pcr_size : 32;
     if (pcr != 2 && pcr != 4 && pcr != 8 && pcr != 16 && pcr != 32) { why = "pcr_size must be 2..32, a power of two"; return ADI_EINVAL; }
     if (x_smem_bytes(spc, tsys, P.fp64x) > 200 * 1024) { why = "x sweep shared memory too large"; return ADI_EUNSUPPORTED; }

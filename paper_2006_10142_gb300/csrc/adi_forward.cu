@@ -138,7 +138,12 @@ __global__ void __launch_bounds__(MAXT, 1) y_sweep_kernel(const YArgs a) {
   const int col = tid & (W - 1);
   const int q = tid >> a.log2W;
   int rank = 0;
-  if (C > 1) rank = (int)cg::this_cluster().block_rank();
+  if (C > 1) {
+    rank = (int)cg::this_cluster().block_rank();
+    // Distributed shared memory may only be touched once every CTA of the
+    // cluster is running: arrive now, wait just before the first remote write.
+    asm volatile("barrier.cluster.arrive.relaxed;" ::: "memory");
+  }
   const int strip = blockIdx.x / C;
   const int gq = rank * tcol + q;
   const int N = 2 * C * tcol;
@@ -170,6 +175,7 @@ __global__ void __launch_bounds__(MAXT, 1) y_sweep_kernel(const YArgs a) {
   Eq<T>* dst = red + (size_t)slot * N + 2 * gq;
   if (C > 1) {
     cg::cluster_group cl = cg::this_cluster();
+    asm volatile("barrier.cluster.wait;" ::: "memory");
     dst = cl.map_shared_rank(dst, owner);
     dst[0] = e0;
     dst[1] = e1;
@@ -298,6 +304,7 @@ size_t y_smem_bytes(int W, int C, int tcol, bool fp64) {
 template <int K, typename T, int MAXT>
 static cudaError_t launch_x_t(const XArgs& a, cudaStream_t st) {
   const int threads = a.spc << a.log2tsys;
+  if (threads % 32 != 0 || threads > MAXT) return cudaErrorInvalidValue;  // whole warps only
   const int blocks = (a.ny + a.spc - 1) / a.spc;
   const size_t sm = x_smem_bytes(a.spc, 1 << a.log2tsys, sizeof(T) == 8);
   x_sweep_kernel<K, T, MAXT><<<blocks, threads, sm, st>>>(a);
@@ -327,6 +334,7 @@ template <int K, typename T, int MAXT>
 static cudaError_t launch_y_t(const YArgs& a, cudaStream_t st) {
   const int W = 1 << a.log2W;
   const int threads = W << a.log2tcol;
+  if (threads % 32 != 0 || threads > MAXT) return cudaErrorInvalidValue;  // whole warps only
   const int strips = (a.nx + W - 1) / W;
   const size_t sm = y_smem_bytes(W, a.C, 1 << a.log2tcol, sizeof(T) == 8);
   cudaLaunchConfig_t cfg = {};

@@ -43,10 +43,13 @@ def _one_step_parity(h, prob, wav):
                           uc.double().cpu().numpy(), hx, hx, prob.tau, wv=wv, src=prob.src,
                           threads=THREADS)
     got = un.double().cpu().numpy()
-    # the increment z = u^{k+1} - 2u^k + u^{k-1} is what the step computes
+    # the increment z = u^{k+1} - 2u^k + u^{k-1} is what the step computes; seen
+    # through the FP32-stored u^{k+1} it carries that field's rounding, so its
+    # error is measured against eps32 |u^{k+1}| as well as |z|
     z_ref = ref - 2 * uc.double().cpu().numpy() + up.double().cpu().numpy()
     z_got = got - 2 * uc.double().cpu().numpy() + up.double().cpu().numpy()
-    return rel_l2(got, ref), rel_l2(z_got, z_ref)
+    scale = 1e-4 * np.linalg.norm(z_ref) + 8 * 2.0 ** -24 * np.linalg.norm(ref)
+    return rel_l2(got, ref), float(np.linalg.norm(z_got - z_ref) / scale)
 
 
 def test_ricker_4096_1000_steps():
@@ -65,7 +68,7 @@ def test_ricker_4096_1000_steps():
     h.run(1000 - 60, src=prob.src, wavelet=wav)
     h.sync_status()
     e_u, e_z = _one_step_parity(h, prob, wav)
-    assert e_u < 1e-5 and e_z < 1e-4, (e_u, e_z)
+    assert e_u < 1e-6 and e_z < 1.0, (e_u, e_z)
     _, uc, k = h.state()
     assert k == 1002
     assert float(uc.abs().max()) > 0
@@ -78,5 +81,5 @@ def test_ricker_16384_200_steps():
     h.run(200, src=prob.src, wavelet=wav)
     h.sync_status()
     e_u, e_z = _one_step_parity(h, prob, wav)
-    assert e_u < 1e-5 and e_z < 1e-4, (e_u, e_z)
+    assert e_u < 1e-6 and e_z < 1.0, (e_u, e_z)
     h.close()
