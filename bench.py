@@ -251,8 +251,8 @@ def main():
     stream = torch.cuda.current_stream()
     h.profile(True)
     h.profile_read()
-    clocks = ClockSampler(torch.cuda.get_device_properties(dev).uuid if hasattr(
-        torch.cuda.get_device_properties(dev), "uuid") else local_rank)
+    vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    clocks = ClockSampler(vis[local_rank].strip() if local_rank < len(vis) else local_rank)
     if rank == 0:
         clocks.start()
         time.sleep(0.5)

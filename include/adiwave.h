@@ -187,17 +187,25 @@ const char *adi_wave_last_error(const adi_wave *h);
  * rows_per_cta:     systems (grid rows) solved by one CTA in the x sweep;
  * cols_per_cta:     columns of the strip one CTA (cluster) solves in the
  *                   y sweep (8, 16 or 32);
- * pcr_size:         size of the interface system handed from cyclic
- *                   reduction to warp-shuffle parallel cyclic reduction
- *                   (2, 4, 8, 16 or 32; the CR-to-PCR switch level);
- * use_graph:        1 = replay steps from a captured CUDA graph.
+ * pcr_size:         ADI_SOLVER_CR_SMEM only: size of the interface system
+ *                   handed from cyclic reduction in shared memory to
+ *                   warp-shuffle parallel cyclic reduction (2, 4, 8, 16 or
+ *                   32; the CR-to-PCR switch level);
+ * use_graph:        1 = replay steps from a captured CUDA graph, -1 = never;
+ * solver:           ADI_SOLVER_TREE (cyclic reduction of the interface
+ *                   system across warp lanes by register shuffles, PCR of the
+ *                   warp summaries) or ADI_SOLVER_CR_SMEM (cyclic reduction
+ *                   level by level in shared memory, PCR for the last
+ *                   `pcr_size` equations).
  * Zero fields mean "choose automatically". */
+enum { ADI_SOLVER_AUTO = 0, ADI_SOLVER_TREE = 1, ADI_SOLVER_CR_SMEM = 2 };
 typedef struct {
     int32_t chunk_x, chunk_y;
     int32_t rows_per_cta;
     int32_t cols_per_cta;
     int32_t pcr_size;
     int32_t use_graph;
+    int32_t solver;
 } adi_wave_tuning;
 
 int adi_wave_get_tuning(const adi_wave *h, adi_wave_tuning *t);

@@ -26,6 +26,10 @@ ADI_FP64_AUTO = 0
 ADI_FP64_NEVER = 1
 ADI_FP64_ALWAYS = 2
 
+ADI_SOLVER_AUTO = 0
+ADI_SOLVER_TREE = 1
+ADI_SOLVER_CR_SMEM = 2
+
 ADI_KERNEL_X = 0
 ADI_KERNEL_Y = 1
 ADI_KERNEL_OTHER = 2
@@ -55,7 +59,8 @@ class Source(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("chunk_x", ctypes.c_int32), ("chunk_y", ctypes.c_int32),
                 ("rows_per_cta", ctypes.c_int32), ("cols_per_cta", ctypes.c_int32),
-                ("pcr_size", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+                ("pcr_size", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("solver", ctypes.c_int32)]
 
 
 class AdiError(RuntimeError):

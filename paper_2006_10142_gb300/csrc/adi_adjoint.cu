@@ -1,0 +1,285 @@
+// adi_adjoint.cu -- kernels of the reverse (adjoint) time step.
+//
+// Forward step k (Eq. CN1 in delta form, factored as in Section 2):
+//   r = tau^2 (m Lap u^k + f^k),  X w = r,  Y z = w,  u^{k+1} = 2u^k - u^{k-1} + z,
+// with X = I - S Lap_x, Y = I - S Lap_y, S = diag(sigma), sigma = tau^2 m / 2.
+// Reverse step (lam^j = dJ/du^j, accumulated from later steps and from the
+// receiver residuals):
+//   zbar = lam^{k+1};   Y^T wbar = zbar;   X^T rbar = wbar;
+//   dJ/dm += (tau^2/2)(wbar . Lap_y z + rbar . Lap_x w) + tau^2 rbar . Lap u^k
+//   lam^k += 2 zbar + tau^2 Lap(m . rbar);   lam^{k-1} -= zbar;
+//   dJ/dw(t_k) += tau^2 rbar_src / (h1 h2).
+// The transposed systems are solved with the forward line solvers through
+// the similarity Y^T = S^{-1} Y S (Lap_y is symmetric):
+//   wbar = m^{-1} . Y^{-1} (m . zbar),   rbar = m^{-1} . X^{-1} (m . wbar)
+// (sigma is m times a constant, which cancels).  The gradient terms are
+// pointwise through the forward identities Y z = w, X w = r:
+//   (tau^2/2) Lap_y z = (z - w)/m,  (tau^2/2) Lap_x w = (w - r)/m,
+//   tau^2 Lap u^k = (r - tau^2 f)/m,
+// so  dJ/dm += (wbar (z - w) + rbar (w - tau^2 f)) / m,
+// accumulated in FP64.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "adi_adjoint.h"
+#include "adi_device.cuh"
+#include "adi_sweeps.cuh"
+
+namespace adi {
+
+// Y^T wbar = lam (column solves): d = m . lam, solve with Y, wbar = x / m.
+template <int K, typename T, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) y_adj_kernel(const YAdjArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int W = 1 << a.log2W;
+  const int tcol = 1 << a.log2tcol;
+  const int C = a.C;
+  cluster_arrive_early(C);
+  const int tid = threadIdx.x;
+  const int col = tid & (W - 1);
+  const int q = tid >> a.log2W;
+  const int rank = cluster_rank(C);
+  const int strip = blockIdx.x / C;
+  const int gq = rank * tcol + q;
+  const int i = strip * W + col;
+  const int j0 = gq * K;
+  const bool colok = i < a.nx;
+  const T sc = (T)a.sc;
+  T d[K], s[K], mm[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int r = j0 + k;
+    const bool ok = colok && r < a.ny;
+    const size_t idx = (size_t)r * a.ld + i;
+    mm[k] = ok ? (T)__ldg(a.m + idx) : T(1);
+    d[k] = ok ? mm[k] * (T)__ldg(a.lam + idx) : T(0);
+    s[k] = ok ? sc * mm[k] : T(0);
+  }
+  y_solve_cols<K, T, true>(smem, a.log2W, a.log2tcol, C, rank, a.pcr, col, gq, d, s);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int r = j0 + k;
+    if (colok && r < a.ny) a.wbar[(size_t)r * a.ld + i] = (float)(d[k] / mm[k]);
+  }
+}
+
+// X^T rbar = wbar (row solves) fused with the FP64 gradient accumulation and
+// the wavelet gradient at the source node.
+template <int K, typename T, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) x_adj_kernel(const XAdjArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tsys = 1 << a.log2tsys;
+  const int tid = threadIdx.x;
+  const int sys = tid >> a.log2tsys;
+  const int p = tid & (tsys - 1);
+  const int j = blockIdx.x * a.spc + sys;
+  const int i0 = p * K;
+  const bool active = (j < a.ny) && (i0 < a.nx);
+  const size_t row = (size_t)j * a.ld;
+  const T sc = (T)a.sc;
+  T d[K], s[K];
+  if (active) {
+    float mv[K], wb[K];
+    load_vec<K>(mv, a.m + row + i0);
+    load_vec<K>(wb, a.wbar + row + i0);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const bool ok = (i0 + k) < a.nx;
+      d[k] = ok ? (T)mv[k] * (T)wb[k] : T(0);
+      s[k] = ok ? sc * (T)mv[k] : T(0);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < K; ++k) { d[k] = T(0); s[k] = T(0); }
+  }
+  x_solve_rows<K, T, true>(smem, a.spc, a.log2tsys, a.pcr, sys, p, d, s);
+  if (!active) return;
+  float mv[K], wb[K], wf[K], zf[K];
+  load_vec<K>(mv, a.m + row + i0);
+  load_vec<K>(wb, a.wbar + row + i0);
+  load_vec<K>(wf, a.w + row + i0);
+  load_vec<K>(zf, a.z + row + i0);
+  float rb[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) rb[k] = ((i0 + k) < a.nx) ? (float)(d[k] / (T)mv[k]) : 0.f;
+  store_vec<K, float>(a.rbar + row + i0, rb);
+  const bool has_src = (j == a.src_iy) && a.src_ix >= i0 && a.src_ix < i0 + K;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if ((i0 + k) >= a.nx) continue;
+    const double r_ = (double)d[k] / (double)mv[k];
+    double wsrc = (double)wf[k];
+    if (has_src && i0 + k == a.src_ix && a.wavelet != nullptr && a.level >= 0 &&
+        a.level < a.n_wavelet)
+      wsrc -= a.src_scale * (double)a.wavelet[a.level];  // tau^2 f^k at the source
+    const double inc = ((double)wb[k] * ((double)zf[k] - (double)wf[k]) + r_ * wsrc) / (double)mv[k];
+    a.gm[(size_t)j * a.nx + i0 + k] += inc;
+    if (has_src && i0 + k == a.src_ix && a.gw != nullptr && a.level >= 0 && a.level < a.n_wavelet)
+      a.gw[a.level] += (float)(a.src_scale * r_);
+  }
+}
+
+// lam^k += 2 lam^{k+1} + tau^2 Lap(m . rbar);  lam^{k-1} -= lam^{k+1};  lam^{k+1} = 0.
+__global__ void lam_update_kernel(LamArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= a.nx || j >= a.ny) return;
+  const size_t c = (size_t)j * a.ld + i;
+  const float mr = __ldg(a.m + c) * __ldg(a.rbar + c);
+  const float l = (i > 0) ? __ldg(a.m + c - 1) * __ldg(a.rbar + c - 1) : 0.f;
+  const float r = (i + 1 < a.nx) ? __ldg(a.m + c + 1) * __ldg(a.rbar + c + 1) : 0.f;
+  const float dn = (j > 0) ? __ldg(a.m + c - a.ld) * __ldg(a.rbar + c - a.ld) : 0.f;
+  const float up = (j + 1 < a.ny) ? __ldg(a.m + c + a.ld) * __ldg(a.rbar + c + a.ld) : 0.f;
+  const float lap = a.cx * (l + r - 2.f * mr) + a.cy * (dn + up - 2.f * mr);
+  const float zb = a.L0[c];
+  a.L1[c] += 2.f * zb + lap;
+  a.L2[c] -= zb;
+  a.L0[c] = 0.f;
+}
+
+// lam[rec r] += resid[s][r] (receivers may share a node, hence the atomics).
+__global__ void seed_kernel(float* lam, int ld, const int* rec, int n_rec, const float* resid) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rec) return;
+  atomicAdd(lam + (size_t)rec[2 * r + 1] * ld + rec[2 * r], resid[r]);
+}
+
+// Start-up dependence (second-order start u^1 = phi + tau psi + tau^2/2 (m Lap phi + f^0)):
+// dJ/dm += (tau^2/2) lam^1 . Lap phi, dJ/dw(t_0) += (tau^2/2) lam^1_src / (h1 h2).
+__global__ void taylor_adj_kernel(TaylorArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= a.nx || j >= a.ny) return;
+  const size_t c = (size_t)j * a.ld + i;
+  const double ph = a.phi[c];
+  const double l = (i > 0) ? a.phi[c - 1] : 0.0;
+  const double r = (i + 1 < a.nx) ? a.phi[c + 1] : 0.0;
+  const double dn = (j > 0) ? a.phi[c - a.ld] : 0.0;
+  const double up = (j + 1 < a.ny) ? a.phi[c + a.ld] : 0.0;
+  const double lam = a.lam[c];
+  a.gm[(size_t)j * a.nx + i] += lam * (a.cx_half * (l + r - 2.0 * ph) + a.cy_half * (dn + up - 2.0 * ph));
+  if (i == a.src_ix && j == a.src_iy && a.gw != nullptr) a.gw[a.level] += (float)(a.src_half * lam);
+}
+
+// ---------------------------------------------------------------------------
+template <int K, typename T, int MAXT>
+static cudaError_t launch_xa_t(const XAdjArgs& a, cudaStream_t st) {
+  const int threads = a.spc << a.log2tsys;
+  if (threads % 32 != 0 || threads > MAXT) return cudaErrorInvalidValue;
+  const int blocks = (a.ny + a.spc - 1) / a.spc;
+  const size_t sm = x_smem_bytes(a.spc, 1 << a.log2tsys, sizeof(T) == 8, true);
+  x_adj_kernel<K, T, MAXT><<<blocks, threads, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int K, typename T, int MAXT>
+static cudaError_t launch_ya_t(const YAdjArgs& a, cudaStream_t st) {
+  const int W = 1 << a.log2W;
+  const int threads = W << a.log2tcol;
+  if (threads % 32 != 0 || threads > MAXT) return cudaErrorInvalidValue;
+  const int strips = (a.nx + W - 1) / W;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(strips * a.C, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = y_smem_bytes(W, a.C, 1 << a.log2tcol, sizeof(T) == 8, true);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = a.C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, y_adj_kernel<K, T, MAXT>, a);
+}
+
+cudaError_t launch_x_adj(const XAdjArgs& a, int K, bool fp64, cudaStream_t st) {
+  if (fp64) {
+    switch (K) {
+      case 4: return launch_xa_t<4, double, 512>(a, st);
+      case 8: return launch_xa_t<8, double, 512>(a, st);
+      case 16: return launch_xa_t<16, double, 512>(a, st);
+      case 32: return launch_xa_t<32, double, 512>(a, st);
+    }
+  } else {
+    switch (K) {
+      case 4: return launch_xa_t<4, float, 1024>(a, st);
+      case 8: return launch_xa_t<8, float, 1024>(a, st);
+      case 16: return launch_xa_t<16, float, 1024>(a, st);
+      case 32: return launch_xa_t<32, float, 1024>(a, st);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_y_adj(const YAdjArgs& a, int K, bool fp64, cudaStream_t st) {
+  if (fp64) {
+    switch (K) {
+      case 4: return launch_ya_t<4, double, 512>(a, st);
+      case 8: return launch_ya_t<8, double, 512>(a, st);
+      case 16: return launch_ya_t<16, double, 512>(a, st);
+      case 32: return launch_ya_t<32, double, 512>(a, st);
+    }
+  } else {
+    switch (K) {
+      case 4: return launch_ya_t<4, float, 1024>(a, st);
+      case 8: return launch_ya_t<8, float, 1024>(a, st);
+      case 16: return launch_ya_t<16, float, 1024>(a, st);
+      case 32: return launch_ya_t<32, float, 1024>(a, st);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_lam_update(const LamArgs& a, cudaStream_t st) {
+  dim3 block(256, 1, 1), grid((a.nx + 255) / 256, a.ny, 1);
+  lam_update_kernel<<<grid, block, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seed(float* lam, int ld, const int* rec, int n_rec, const float* resid,
+                        cudaStream_t st) {
+  if (n_rec <= 0) return cudaSuccess;
+  seed_kernel<<<(n_rec + 127) / 128, 128, 0, st>>>(lam, ld, rec, n_rec, resid);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_taylor_adj(const TaylorArgs& a, cudaStream_t st) {
+  dim3 block(256, 1, 1), grid((a.nx + 255) / 256, a.ny, 1);
+  taylor_adj_kernel<<<grid, block, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename KernT>
+static cudaError_t allow_smem(KernT kern) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+
+cudaError_t configure_adjoint_kernels() {
+  cudaError_t e = cudaSuccess;
+#define ADI_CFG(kern) \
+  if (e == cudaSuccess) e = allow_smem(kern);
+  ADI_CFG((x_adj_kernel<4, float, 1024>))
+  ADI_CFG((x_adj_kernel<8, float, 1024>))
+  ADI_CFG((x_adj_kernel<16, float, 1024>))
+  ADI_CFG((x_adj_kernel<32, float, 1024>))
+  ADI_CFG((x_adj_kernel<4, double, 512>))
+  ADI_CFG((x_adj_kernel<8, double, 512>))
+  ADI_CFG((x_adj_kernel<16, double, 512>))
+  ADI_CFG((x_adj_kernel<32, double, 512>))
+  ADI_CFG((y_adj_kernel<4, float, 1024>))
+  ADI_CFG((y_adj_kernel<8, float, 1024>))
+  ADI_CFG((y_adj_kernel<16, float, 1024>))
+  ADI_CFG((y_adj_kernel<32, float, 1024>))
+  ADI_CFG((y_adj_kernel<4, double, 512>))
+  ADI_CFG((y_adj_kernel<8, double, 512>))
+  ADI_CFG((y_adj_kernel<16, double, 512>))
+  ADI_CFG((y_adj_kernel<32, double, 512>))
+#undef ADI_CFG
+  return e;
+}
+
+}  // namespace adi

@@ -56,9 +56,14 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
   // dominance ratio (|a| + |c|) / |b| = 2s / (1 + 2s); weak above 0.9
   const bool weak_x = 2.0 * sxm / (1.0 + 2.0 * sxm) > kWeakDominance;
   const bool weak_y = 2.0 * sym / (1.0 + 2.0 * sym) > kWeakDominance;
-  GridPlan& P = G.plan;
+  GridPlan P = G.plan;
   P.fp64x = G.fp64mode == ADI_FP64_ALWAYS || (G.fp64mode == ADI_FP64_AUTO && weak_x);
   P.fp64y = G.fp64mode == ADI_FP64_ALWAYS || (G.fp64mode == ADI_FP64_AUTO && weak_y);
+  if (t.solver < ADI_SOLVER_AUTO || t.solver > ADI_SOLVER_CR_SMEM) { why = "unknown solver"; return ADI_EINVAL; }
+  P.tree = t.solver != ADI_SOLVER_CR_SMEM;
+  int pcr = t.pcr_size ? t.pcr_size : 32;
+  if (pcr != 2 && pcr != 4 && pcr != 8 && pcr != 16 && pcr != 32) { why = "pcr_size must be 2..32, a power of two"; return ADI_EINVAL; }
+  P.pcr = pcr;
 
   // ---- x sweep
   {
@@ -78,39 +83,53 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
       spc = (spc + q - 1) / q * q;
       if (spc * tsys > maxT) spc = maxT / tsys;
     }
-    int pcr = t.pcr_size ? t.pcr_size : 32;
-    if (pcr != 2 && pcr != 4 && pcr != 8 && pcr != 16 && pcr != 32) { why = "pcr_size must be 2..32, a power of two"; return ADI_EINVAL; }
-    if (x_smem_bytes(spc, tsys, P.fp64x) > 200 * 1024) { why = "x sweep shared memory too large"; return ADI_EUNSUPPORTED; }
+    if (x_smem_bytes(spc, tsys, P.fp64x, P.tree) > 200 * 1024) { why = "x sweep shared memory too large"; return ADI_EUNSUPPORTED; }
     P.kx = K;
     P.log2tsys = ilog2(tsys);
     P.spc = spc;
-    P.pcr = pcr;
   }
   // ---- y sweep
   {
     const int maxT = P.fp64y ? 512 : 1024;
+    const int maxC = 16;
     int W = t.cols_per_cta ? t.cols_per_cta : 8;
     if (W != 4 && W != 8 && W != 16 && W != 32) { why = "cols_per_cta must be 4, 8, 16 or 32"; return ADI_EINVAL; }
+    auto geom = [&](int K, int& tcol, int& C) {
+      const int ttot = next_pow2((G.ny + K - 1) / K);
+      tcol = std::min(ttot, maxT / W);
+      if (W * tcol < 32) tcol = 32 / W;  // whole warps; extra chunks are empty rows
+      C = std::max(1, ttot / tcol);
+    };
+    // the tree's top system holds at most 32 warp groups per column
+    auto fits = [&](int K) {
+      int tcol, C;
+      geom(K, tcol, C);
+      const int groups = C * std::max(1, tcol / 32);
+      return C <= maxC && (!P.tree || groups <= 32);
+    };
     int K = t.chunk_y;
-    const int maxC = 16;
     if (K == 0) {
       K = P.fp64y ? 8 : (G.ny >= 64 ? 8 : 4);
-      // prefer portable clusters (<= 8 CTAs)
-      while (K < 32 && next_pow2((G.ny + K - 1) / K) / std::min(next_pow2((G.ny + K - 1) / K), maxT / W) > 8) K *= 2;
+      // prefer portable clusters (<= 8 CTAs) and a top system that fits a warp
+      while (K < 32) {
+        int tcol, C;
+        geom(K, tcol, C);
+        if (C <= 8 && fits(K)) break;
+        K *= 2;
+      }
     }
     if (K != 4 && K != 8 && K != 16 && K != 32) { why = "chunk_y must be 4, 8, 16 or 32"; return ADI_EINVAL; }
-    const int ttot = next_pow2((G.ny + K - 1) / K);
-    int tcol = std::min(ttot, maxT / W);
-    if (W * tcol < 32) tcol = 32 / W;  // whole warps; extra chunks are empty rows
-    const int C = std::max(1, ttot / tcol);
-    if (C > maxC) { why = "ny too large for a 16-CTA cluster"; return ADI_EUNSUPPORTED; }
-    if (y_smem_bytes(W, C, tcol, P.fp64y) > 200 * 1024) { why = "y sweep shared memory too large"; return ADI_EUNSUPPORTED; }
+    int tcol, C;
+    geom(K, tcol, C);
+    if (!fits(K)) { why = "ny too large for this chunk_y (cluster or top system)"; return ADI_EUNSUPPORTED; }
+    if (y_smem_bytes(W, C, tcol, P.fp64y, P.tree) > 200 * 1024) { why = "y sweep shared memory too large"; return ADI_EUNSUPPORTED; }
     P.ky = K;
     P.log2W = ilog2(W);
     P.log2tcol = ilog2(tcol);
     P.C = C;
   }
-  P.graph = (t.use_graph == 0) ? 1 : (t.use_graph > 0 ? 1 : 0);
+  P.graph = (t.use_graph >= 0) ? 1 : 0;
+  G.plan = P;
   return ADI_OK;
 }
 
@@ -238,6 +257,7 @@ extern "C" int adi_wave_get_tuning(const adi_wave* h, adi_wave_tuning* t) {
   t->cols_per_cta = 1 << P.log2W;
   t->pcr_size = P.pcr;
   t->use_graph = P.graph ? 1 : -1;
+  t->solver = P.tree ? ADI_SOLVER_TREE : ADI_SOLVER_CR_SMEM;
   return ADI_OK;
 }
 

@@ -73,6 +73,18 @@ template <typename T> __device__ __forceinline__ T shfl_up_t(T v, int s) {
 template <typename T> __device__ __forceinline__ T shfl_down_t(T v, int s) {
   return __shfl_down_sync(0xffffffffu, v, s);
 }
+template <typename T> __device__ __forceinline__ Eq<T> shfl_up_eq(const Eq<T>& e, int s) {
+  Eq<T> r;
+  r.a = __shfl_up_sync(0xffffffffu, e.a, s); r.b = __shfl_up_sync(0xffffffffu, e.b, s);
+  r.c = __shfl_up_sync(0xffffffffu, e.c, s); r.d = __shfl_up_sync(0xffffffffu, e.d, s);
+  return r;
+}
+template <typename T> __device__ __forceinline__ Eq<T> shfl_down_eq(const Eq<T>& e, int s) {
+  Eq<T> r;
+  r.a = __shfl_down_sync(0xffffffffu, e.a, s); r.b = __shfl_down_sync(0xffffffffu, e.b, s);
+  r.c = __shfl_down_sync(0xffffffffu, e.c, s); r.d = __shfl_down_sync(0xffffffffu, e.d, s);
+  return r;
+}
 
 // -------------------------------------------------------------------------
 // 1. partition step on K consecutive unknowns held by one thread
@@ -225,6 +237,141 @@ __device__ void reduced_solve(Eq<T>* red, T* xs, int nsys, int N, int log2N, int
       X[i] = div_t(e.d - e.a * xl - e.c * xr, e.b);
     }
     __syncthreads();
+  }
+}
+
+}  // namespace adi
+
+namespace adi {
+
+// -------------------------------------------------------------------------
+// Block cyclic reduction of the interface system across the lanes of a warp
+// -------------------------------------------------------------------------
+// A segment [a, c] of consecutive unknowns is summarised by two equations:
+//   f:  A x_{a-1} + B x_a + C x_c     = D
+//   l:  A x_a     + B x_c + C x_{c+1} = D
+// (a chunk's interface equations e0, e1 are such a summary).  Merging the
+// adjacent segments L = [a, b] and R = [b+1, c] eliminates the interface
+// unknowns x_b and x_{b+1} between them -- one level of cyclic reduction on
+// the interface system -- and leaves the summary of [a, c].  The node keeps
+//   x_b     = xb0 + xba x_a + xbc x_c,   x_{b+1} = y0 + yba x_a + ybc x_c
+// for the back substitution.
+template <typename T> struct Seg {
+  Eq<T> f, l;
+};
+
+template <typename T> struct Node {
+  T xb0, xba, xbc, y0, yba, ybc;
+};
+
+template <typename T>
+__device__ __forceinline__ Seg<T> seg_merge(const Seg<T>& L, const Seg<T>& R, Node<T>& nd) {
+  const T idet = rcp_t(L.l.b * R.f.b - L.l.c * R.f.a);
+  nd.xb0 = (R.f.b * L.l.d - L.l.c * R.f.d) * idet;
+  nd.xba = -(R.f.b * L.l.a) * idet;
+  nd.xbc = (L.l.c * R.f.c) * idet;
+  nd.y0 = (L.l.b * R.f.d - R.f.a * L.l.d) * idet;
+  nd.yba = (R.f.a * L.l.a) * idet;
+  nd.ybc = -(L.l.b * R.f.c) * idet;
+  Seg<T> S;
+  S.f.a = L.f.a;
+  S.f.b = fma(L.f.c, nd.xba, L.f.b);
+  S.f.c = L.f.c * nd.xbc;
+  S.f.d = fma(-L.f.c, nd.xb0, L.f.d);
+  S.l.a = R.l.a * nd.yba;
+  S.l.b = fma(R.l.a, nd.ybc, R.l.b);
+  S.l.c = R.l.c;
+  S.l.d = fma(-R.l.a, nd.y0, R.l.d);
+  return S;
+}
+
+template <typename T> __device__ __forceinline__ Eq<T> shfl_xor_eq(const Eq<T>& e, int m) {
+  Eq<T> r;
+  r.a = __shfl_xor_sync(0xffffffffu, e.a, m);
+  r.b = __shfl_xor_sync(0xffffffffu, e.b, m);
+  r.c = __shfl_xor_sync(0xffffffffu, e.c, m);
+  r.d = __shfl_xor_sync(0xffffffffu, e.d, m);
+  return r;
+}
+
+// Node slot of level t for the group of `lane` (31 slots per warp: 16 nodes
+// at level 0, 8 at level 1, ...).
+__device__ __forceinline__ int node_slot(int t, int lane) {
+  return (32 - (32 >> t)) + (lane >> (t + 1));
+}
+
+// Up-sweep: merge the lanes' segments pairwise over `levels` levels (groups
+// of 2^levels consecutive lanes).  Every lane of a group ends with the
+// group's summary; node data go to nodes[0..30] (one warp's slots).
+template <typename T>
+__device__ __forceinline__ Seg<T> warp_tree_up(Seg<T> S, Node<T>* nodes, int lane, int levels) {
+  for (int t = 0; t < levels; ++t) {
+    const int m = 1 << t;
+    Seg<T> P;
+    P.f = shfl_xor_eq(S.f, m);
+    P.l = shfl_xor_eq(S.l, m);
+    Node<T> nd;
+    if (lane & m) S = seg_merge(P, S, nd);
+    else S = seg_merge(S, P, nd);
+    if ((lane & (2 * m - 1)) == 0) nodes[node_slot(t, lane)] = nd;
+  }
+  __syncwarp();
+  return S;
+}
+
+// Down-sweep: from the group's outer values (xa, xc) to this lane's segment
+// end values.
+template <typename T>
+__device__ __forceinline__ void warp_tree_down(const Node<T>* nodes, int lane, int levels, T& xa,
+                                               T& xc) {
+  for (int t = levels - 1; t >= 0; --t) {
+    const Node<T> nd = nodes[node_slot(t, lane)];
+    if (lane & (1 << t)) xa = fma(nd.ybc, xc, fma(nd.yba, xa, nd.y0));
+    else xc = fma(nd.xbc, xc, fma(nd.xba, xa, nd.xb0));
+  }
+}
+
+// Both end values of a summarised segment whose outside neighbours are zero.
+template <typename T>
+__device__ __forceinline__ void seg_solve_closed(const Seg<T>& S, T& xa, T& xc) {
+  // f: B xa + C xc = D ;  l: A xa + B xc = D
+  const T idet = rcp_t(S.f.b * S.l.b - S.f.c * S.l.a);
+  xa = (S.f.d * S.l.b - S.f.c * S.l.d) * idet;
+  xc = (S.f.b * S.l.d - S.l.a * S.f.d) * idet;
+}
+
+// Parallel cyclic reduction of up to 64 equations in one warp, lane l holding
+// equations 2l (E0) and 2l+1 (E1); n_eq = number of real equations (lanes
+// beyond hold identities).  On return E0.d / E0.b and E1.d / E1.b are the
+// solution.  Unknowns outside 0..n_eq-1 are zero.
+template <typename T>
+__device__ __forceinline__ void pcr64(Eq<T>& E0, Eq<T>& E1, int lane, int n_eq) {
+  const Eq<T> I = eq_identity<T>();
+  // distance 1
+  {
+    Eq<T> prev1 = shfl_up_eq(E1, 1);      // equation 2l - 1
+    Eq<T> next0 = shfl_down_eq(E0, 1);    // equation 2l + 2
+    if (lane == 0) prev1 = I;
+    if (2 * lane + 2 >= n_eq) next0 = I;
+    const Eq<T> e1hi = (2 * lane + 1 < n_eq) ? E1 : I;
+    const Eq<T> n0 = cr_combine(E0, prev1, e1hi);
+    const Eq<T> n1 = cr_combine(E1, E0, next0);
+    E0 = n0;
+    E1 = n1;
+  }
+  // distances 2, 4, ..., 32 (lane offsets 1, 2, ..., 16)
+  for (int h = 1; h < 32; h <<= 1) {
+    const int s = 2 * h;
+    Eq<T> lo0 = shfl_up_eq(E0, h), lo1 = shfl_up_eq(E1, h);
+    Eq<T> hi0 = shfl_down_eq(E0, h), hi1 = shfl_down_eq(E1, h);
+    if (2 * lane - s < 0) lo0 = I;
+    if (2 * lane + 1 - s < 0) lo1 = I;
+    if (2 * lane + s >= n_eq || lane + h >= 32) hi0 = I;
+    if (2 * lane + 1 + s >= n_eq || lane + h >= 32) hi1 = I;
+    const Eq<T> n0 = cr_combine(E0, lo0, hi0);
+    const Eq<T> n1 = cr_combine(E1, lo1, hi1);
+    E0 = n0;
+    E1 = n1;
   }
 }
 

@@ -6,52 +6,28 @@
 //   pass 2, y_sweep_kernel: the column solves Y z = w, Y = I - S Lap_y
 //           (Eq. fr2's operator), fused with u^{k+1} = 2u^k - u^{k-1} + z,
 //           written over u^{k-1} (the buffer swap of Algorithm 1).
-// Both solve their lines with the partition + CR + PCR scheme of
-// adi_device.cuh.  Memory traffic per grid point: pass 1 reads u^k and m
-// and writes w (12 B, plus halo rows served by L2); pass 2 reads w, m, u^k,
-// u^{k-1} and writes u^{k+1} (20 B).
-#include <cooperative_groups.h>
+// Both solve their lines with the cores of adi_sweeps.cuh.  Memory traffic
+// per grid point: pass 1 reads u^k and m and writes w (12 B, plus halo rows
+// served by L2); pass 2 reads w, m, u^k, u^{k-1} and writes u^{k+1} (20 B).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "adi_device.cuh"
 #include "adi_internal.h"
-
-namespace cg = cooperative_groups;
+#include "adi_sweeps.cuh"
 
 namespace adi {
-
-template <int K>
-__device__ __forceinline__ void load_vec(float (&v)[K], const float* __restrict__ p) {
-  const float4* p4 = reinterpret_cast<const float4*>(p);
-#pragma unroll
-  for (int q = 0; q < K / 4; ++q) {
-    float4 t = __ldg(p4 + q);
-    v[4 * q + 0] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
-  }
-}
-
-template <int K, typename T>
-__device__ __forceinline__ void store_vec(float* __restrict__ p, const T (&v)[K]) {
-  float4* p4 = reinterpret_cast<float4*>(p);
-#pragma unroll
-  for (int q = 0; q < K / 4; ++q)
-    p4[q] = make_float4((float)v[4 * q + 0], (float)v[4 * q + 1], (float)v[4 * q + 2],
-                        (float)v[4 * q + 3]);
-}
 
 // ---------------------------------------------------------------------------
 // pass 1: RHS assembly + x solve.  CTA = `spc` rows, 2^log2tsys threads per
 // row, K contiguous unknowns per thread.
 // ---------------------------------------------------------------------------
-template <int K, typename T, int MAXT>
+template <int K, typename T, int MAXT, bool TREE>
 __global__ void __launch_bounds__(MAXT, 1) x_sweep_kernel(const XArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tsys = 1 << a.log2tsys;
-  const int N = 2 * tsys;
-  Eq<T>* red = reinterpret_cast<Eq<T>*>(smem);
-  T* xs = reinterpret_cast<T*>(red + (size_t)a.spc * N);
-
   const int tid = threadIdx.x;
   const int sys = tid >> a.log2tsys;
   const int p = tid & (tsys - 1);
@@ -82,20 +58,20 @@ __global__ void __launch_bounds__(MAXT, 1) x_sweep_kernel(const XArgs a) {
     load_vec<K>(v, a.m + row + i0);
     const float uL = (i0 > 0) ? __ldg(a.u + row + i0 - 1) : 0.f;
     const float uR = (i0 + K < a.nx) ? __ldg(a.u + row + i0 + K) : 0.f;
+    // padding columns (i >= nx) hold zero u and zero m, so r = s = 0 there
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const T c = (T)uc[k];
       const T l = (T)(k > 0 ? uc[k - 1] : uL);
       const T r = (T)(k < K - 1 ? uc[k + 1] : uR);
       const T lap = cx * (l + r - T(2) * c) + cy * (d[k] - T(2) * c);
-      const bool ok = (i0 + k) < a.nx;
-      d[k] = ok ? (T)v[k] * lap : T(0);
-      s[k] = ok ? sc * (T)v[k] : T(0);
+      d[k] = (T)v[k] * lap;
+      s[k] = sc * (T)v[k];
     }
     // point source f^k = w(t_k) / (h1 h2) at one node
     const GridDev* gd = a.gd;
-    const int sx = gd->src_ix, sy = gd->src_iy;
-    if (j == sy && sx >= i0 && sx < i0 + K) {
+    const int sx = gd->src_ix;
+    if (j == gd->src_iy && sx >= i0 && sx < i0 + K) {
       const long long lev = gd->k;
       if (gd->wavelet != nullptr && lev >= 0 && lev < gd->n_wavelet) {
         const T f = (T)a.src_scale * (T)gd->wavelet[lev];
@@ -109,109 +85,73 @@ __global__ void __launch_bounds__(MAXT, 1) x_sweep_kernel(const XArgs a) {
     for (int k = 0; k < K; ++k) { d[k] = T(0); s[k] = T(0); }
   }
 
-  Eq<T> e0, e1;
-  chunk_reduce<K, T>(d, s, e0, e1);
-  red[(size_t)sys * N + 2 * p] = e0;
-  red[(size_t)sys * N + 2 * p + 1] = e1;
-  __syncthreads();
-  reduced_solve<T>(red, xs, a.spc, N, a.log2tsys + 1, a.pcr);
-  const T x0 = xs[(size_t)sys * N + 2 * p];
-  const T xl = xs[(size_t)sys * N + 2 * p + 1];
-  chunk_backsub<K, T>(d, s, x0, xl);
+  x_solve_rows<K, T, TREE>(smem, a.spc, a.log2tsys, a.pcr, sys, p, d, s);
   if (active) store_vec<K, T>(a.w + row + i0, d);
 }
 
 // ---------------------------------------------------------------------------
 // pass 2: y solve + update.  A strip of 2^log2W columns; a cluster of C CTAs
 // covers the whole column length, each CTA 2^log2tcol threads per column
-// with K consecutive rows per thread.  The interface system of column c is
-// gathered into the shared memory of cluster rank (c mod C) over DSMEM,
-// solved there, and the interface values are read back the same way.
+// with K consecutive rows per thread.
 // ---------------------------------------------------------------------------
-template <int K, typename T, int MAXT>
+template <int K, typename T, int MAXT, bool TREE>
 __global__ void __launch_bounds__(MAXT, 1) y_sweep_kernel(const YArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int W = 1 << a.log2W;
   const int tcol = 1 << a.log2tcol;
   const int C = a.C;
+  cluster_arrive_early(C);
   const int tid = threadIdx.x;
   const int col = tid & (W - 1);
   const int q = tid >> a.log2W;
-  int rank = 0;
-  if (C > 1) {
-    rank = (int)cg::this_cluster().block_rank();
-    // Distributed shared memory may only be touched once every CTA of the
-    // cluster is running: arrive now, wait just before the first remote write.
-    asm volatile("barrier.cluster.arrive.relaxed;" ::: "memory");
-  }
+  const int rank = cluster_rank(C);
   const int strip = blockIdx.x / C;
   const int gq = rank * tcol + q;
-  const int N = 2 * C * tcol;
-  int log2N = a.log2tcol + 1;
-  for (int c = C; c > 1; c >>= 1) ++log2N;
-  const int n_slots = (W + C - 1) / C;
-  Eq<T>* red = reinterpret_cast<Eq<T>*>(smem);
-  T* xs = reinterpret_cast<T*>(red + (size_t)n_slots * N);
-  const int owner = col % C;
-  const int slot = col / C;
-
   const int i = strip * W + col;
   const int j0 = gq * K;
   const bool colok = i < a.nx;
+  const bool full = colok && (j0 + K <= a.ny);
+  const size_t ld = (size_t)a.ld;
+  const size_t base = (size_t)j0 * ld + i;
   const T sc = (T)a.sc;
 
   T d[K], s[K];
+  if (full) {
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const int r = j0 + k;
-    const bool ok = colok && r < a.ny;
-    const size_t idx = (size_t)r * a.ld + i;
-    d[k] = ok ? (T)__ldg(a.w + idx) : T(0);
-    s[k] = ok ? sc * (T)__ldg(a.m + idx) : T(0);
-  }
-
-  Eq<T> e0, e1;
-  chunk_reduce<K, T>(d, s, e0, e1);
-  Eq<T>* dst = red + (size_t)slot * N + 2 * gq;
-  if (C > 1) {
-    cg::cluster_group cl = cg::this_cluster();
-    asm volatile("barrier.cluster.wait;" ::: "memory");
-    dst = cl.map_shared_rank(dst, owner);
-    dst[0] = e0;
-    dst[1] = e1;
-    cl.sync();
+    for (int k = 0; k < K; ++k) {
+      d[k] = (T)__ldg(a.w + base + k * ld);
+      s[k] = sc * (T)__ldg(a.m + base + k * ld);
+    }
   } else {
-    dst[0] = e0;
-    dst[1] = e1;
-    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const bool ok = colok && (j0 + k) < a.ny;
+      d[k] = ok ? (T)__ldg(a.w + base + k * ld) : T(0);
+      s[k] = ok ? sc * (T)__ldg(a.m + base + k * ld) : T(0);
+    }
   }
-  const int n_own = (rank < W) ? (W - 1 - rank) / C + 1 : 0;
-  reduced_solve<T>(red, xs, n_own, N, log2N, a.pcr);
-  T x0, xl;
-  if (C > 1) {
-    cg::cluster_group cl = cg::this_cluster();
-    cl.sync();
-    const T* src = cl.map_shared_rank(xs + (size_t)slot * N + 2 * gq, owner);
-    x0 = src[0];
-    xl = src[1];
-    cl.sync();  // owners keep their shared memory until every read is done
-  } else {
-    x0 = xs[(size_t)slot * N + 2 * gq];
-    xl = xs[(size_t)slot * N + 2 * gq + 1];
-  }
-  chunk_backsub<K, T>(d, s, x0, xl);
+  y_solve_cols<K, T, TREE>(smem, a.log2W, a.log2tcol, C, rank, a.pcr, col, gq, d, s);
 
   bool bad = false;
+  if (full) {
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const int r = j0 + k;
-    if (colok && r < a.ny) {
-      const size_t idx = (size_t)r * a.ld + i;
-      const float uc = __ldg(a.u_cur + idx);
-      const float up = a.u_prev[idx];
-      const float un = 2.0f * uc - up + (float)d[k];
+    for (int k = 0; k < K; ++k) {
+      const size_t idx = base + k * ld;
+      const float un = 2.0f * __ldg(a.u_cur + idx) - a.u_prev[idx] + (float)d[k];
       a.u_prev[idx] = un;
+      if (a.z_out) a.z_out[idx] = (float)d[k];
       bad |= !isfinite(un);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (colok && (j0 + k) < a.ny) {
+        const size_t idx = base + k * ld;
+        const float un = 2.0f * __ldg(a.u_cur + idx) - a.u_prev[idx] + (float)d[k];
+        a.u_prev[idx] = un;
+        if (a.z_out) a.z_out[idx] = (float)d[k];
+        bad |= !isfinite(un);
+      }
     }
   }
   if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0 && a.err) atomicOr(a.err, ERR_NUMERIC);
@@ -288,59 +228,48 @@ __global__ void scan_m_kernel(const float* __restrict__ m, int nx, int ny, int l
 // launchers
 // ---------------------------------------------------------------------------
 
-size_t x_smem_bytes(int spc, int tsys, bool fp64) {
+size_t x_smem_bytes(int spc, int tsys, bool fp64, bool tree) {
+  if (tree) {
+    const int nwarps = std::max(1, spc * tsys / 32);
+    return fp64 ? XTreeSmem<double>::bytes(nwarps) : XTreeSmem<float>::bytes(nwarps);
+  }
   const size_t N = 2 * (size_t)tsys;
   return fp64 ? spc * N * (sizeof(Eq<double>) + sizeof(double))
               : spc * N * (sizeof(Eq<float>) + sizeof(float));
 }
 
-size_t y_smem_bytes(int W, int C, int tcol, bool fp64) {
-  const size_t N = 2 * (size_t)C * tcol;
+size_t y_smem_bytes(int W, int C, int tcol, bool fp64, bool tree) {
   const size_t slots = (W + C - 1) / C;
+  if (tree) {
+    const int threads = W * tcol;
+    return fp64 ? YTreeSmem<double>::bytes(threads, (int)slots)
+                : YTreeSmem<float>::bytes(threads, (int)slots);
+  }
+  const size_t N = 2 * (size_t)C * tcol;
   return fp64 ? slots * N * (sizeof(Eq<double>) + sizeof(double))
               : slots * N * (sizeof(Eq<float>) + sizeof(float));
 }
 
-template <int K, typename T, int MAXT>
+template <int K, typename T, int MAXT, bool TREE>
 static cudaError_t launch_x_t(const XArgs& a, cudaStream_t st) {
   const int threads = a.spc << a.log2tsys;
   if (threads % 32 != 0 || threads > MAXT) return cudaErrorInvalidValue;  // whole warps only
   const int blocks = (a.ny + a.spc - 1) / a.spc;
-  const size_t sm = x_smem_bytes(a.spc, 1 << a.log2tsys, sizeof(T) == 8);
-  x_sweep_kernel<K, T, MAXT><<<blocks, threads, sm, st>>>(a);
+  const size_t sm = x_smem_bytes(a.spc, 1 << a.log2tsys, sizeof(T) == 8, TREE);
+  x_sweep_kernel<K, T, MAXT, TREE><<<blocks, threads, sm, st>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_x(const XArgs& a, int K, bool fp64, cudaStream_t st) {
-  if (fp64) {
-    switch (K) {
-      case 4: return launch_x_t<4, double, 512>(a, st);
-      case 8: return launch_x_t<8, double, 512>(a, st);
-      case 16: return launch_x_t<16, double, 512>(a, st);
-      case 32: return launch_x_t<32, double, 512>(a, st);
-    }
-  } else {
-    switch (K) {
-      case 4: return launch_x_t<4, float, 1024>(a, st);
-      case 8: return launch_x_t<8, float, 1024>(a, st);
-      case 16: return launch_x_t<16, float, 1024>(a, st);
-      case 32: return launch_x_t<32, float, 1024>(a, st);
-    }
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <int K, typename T, int MAXT>
+template <int K, typename T, int MAXT, bool TREE>
 static cudaError_t launch_y_t(const YArgs& a, cudaStream_t st) {
   const int W = 1 << a.log2W;
   const int threads = W << a.log2tcol;
   if (threads % 32 != 0 || threads > MAXT) return cudaErrorInvalidValue;  // whole warps only
   const int strips = (a.nx + W - 1) / W;
-  const size_t sm = y_smem_bytes(W, a.C, 1 << a.log2tcol, sizeof(T) == 8);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(strips * a.C, 1, 1);
   cfg.blockDim = dim3(threads, 1, 1);
-  cfg.dynamicSmemBytes = sm;
+  cfg.dynamicSmemBytes = y_smem_bytes(W, a.C, 1 << a.log2tcol, sizeof(T) == 8, TREE);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -349,24 +278,35 @@ static cudaError_t launch_y_t(const YArgs& a, cudaStream_t st) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, y_sweep_kernel<K, T, MAXT>, a);
+  return cudaLaunchKernelEx(&cfg, y_sweep_kernel<K, T, MAXT, TREE>, a);
 }
 
-cudaError_t launch_y(const YArgs& a, int K, bool fp64, cudaStream_t st) {
+#define ADI_DISPATCH_K(FN, TT, MT, TR, ARGS)             \
+  switch (K) {                                           \
+    case 4: return FN<4, TT, MT, TR> ARGS;               \
+    case 8: return FN<8, TT, MT, TR> ARGS;               \
+    case 16: return FN<16, TT, MT, TR> ARGS;             \
+    case 32: return FN<32, TT, MT, TR> ARGS;             \
+  }
+
+cudaError_t launch_x(const XArgs& a, int K, bool fp64, bool tree, cudaStream_t st) {
   if (fp64) {
-    switch (K) {
-      case 4: return launch_y_t<4, double, 512>(a, st);
-      case 8: return launch_y_t<8, double, 512>(a, st);
-      case 16: return launch_y_t<16, double, 512>(a, st);
-      case 32: return launch_y_t<32, double, 512>(a, st);
-    }
+    if (tree) { ADI_DISPATCH_K(launch_x_t, double, 512, true, (a, st)) }
+    else { ADI_DISPATCH_K(launch_x_t, double, 512, false, (a, st)) }
   } else {
-    switch (K) {
-      case 4: return launch_y_t<4, float, 1024>(a, st);
-      case 8: return launch_y_t<8, float, 1024>(a, st);
-      case 16: return launch_y_t<16, float, 1024>(a, st);
-      case 32: return launch_y_t<32, float, 1024>(a, st);
-    }
+    if (tree) { ADI_DISPATCH_K(launch_x_t, float, 1024, true, (a, st)) }
+    else { ADI_DISPATCH_K(launch_x_t, float, 1024, false, (a, st)) }
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_y(const YArgs& a, int K, bool fp64, bool tree, cudaStream_t st) {
+  if (fp64) {
+    if (tree) { ADI_DISPATCH_K(launch_y_t, double, 512, true, (a, st)) }
+    else { ADI_DISPATCH_K(launch_y_t, double, 512, false, (a, st)) }
+  } else {
+    if (tree) { ADI_DISPATCH_K(launch_y_t, float, 1024, true, (a, st)) }
+    else { ADI_DISPATCH_K(launch_y_t, float, 1024, false, (a, st)) }
   }
   return cudaErrorInvalidValue;
 }
@@ -380,27 +320,22 @@ static cudaError_t allow_smem(KernT kern, bool cluster16) {
   return e;
 }
 
+#define ADI_CFG4(KERN, TT, MT, TR, CL)                                   \
+  if (e == cudaSuccess) e = allow_smem(KERN<4, TT, MT, TR>, CL);         \
+  if (e == cudaSuccess) e = allow_smem(KERN<8, TT, MT, TR>, CL);         \
+  if (e == cudaSuccess) e = allow_smem(KERN<16, TT, MT, TR>, CL);        \
+  if (e == cudaSuccess) e = allow_smem(KERN<32, TT, MT, TR>, CL);
+
 cudaError_t configure_kernels() {
   cudaError_t e = cudaSuccess;
-#define ADI_CFG(kern, cl)                       \
-  if (e == cudaSuccess) e = allow_smem(kern, cl);
-  ADI_CFG((x_sweep_kernel<4, float, 1024>), false)
-  ADI_CFG((x_sweep_kernel<8, float, 1024>), false)
-  ADI_CFG((x_sweep_kernel<16, float, 1024>), false)
-  ADI_CFG((x_sweep_kernel<32, float, 1024>), false)
-  ADI_CFG((x_sweep_kernel<4, double, 512>), false)
-  ADI_CFG((x_sweep_kernel<8, double, 512>), false)
-  ADI_CFG((x_sweep_kernel<16, double, 512>), false)
-  ADI_CFG((x_sweep_kernel<32, double, 512>), false)
-  ADI_CFG((y_sweep_kernel<4, float, 1024>), true)
-  ADI_CFG((y_sweep_kernel<8, float, 1024>), true)
-  ADI_CFG((y_sweep_kernel<16, float, 1024>), true)
-  ADI_CFG((y_sweep_kernel<32, float, 1024>), true)
-  ADI_CFG((y_sweep_kernel<4, double, 512>), true)
-  ADI_CFG((y_sweep_kernel<8, double, 512>), true)
-  ADI_CFG((y_sweep_kernel<16, double, 512>), true)
-  ADI_CFG((y_sweep_kernel<32, double, 512>), true)
-#undef ADI_CFG
+  ADI_CFG4(x_sweep_kernel, float, 1024, true, false)
+  ADI_CFG4(x_sweep_kernel, float, 1024, false, false)
+  ADI_CFG4(x_sweep_kernel, double, 512, true, false)
+  ADI_CFG4(x_sweep_kernel, double, 512, false, false)
+  ADI_CFG4(y_sweep_kernel, float, 1024, true, true)
+  ADI_CFG4(y_sweep_kernel, float, 1024, false, true)
+  ADI_CFG4(y_sweep_kernel, double, 512, true, true)
+  ADI_CFG4(y_sweep_kernel, double, 512, false, true)
   return e;
 }
 

@@ -49,14 +49,15 @@ struct YArgs {
   const float* w;      // RHS
   const float* u_cur;  // u^k
   float* u_prev;       // in: u^{k-1}; out: u^{k+1}
+  float* z_out;        // optional copy of z = u^{k+1} - 2u^k + u^{k-1} (adjoint recompute)
   double sc;           // tau^2 / (2 h2^2)
   GridDev* gd;         // k is advanced by one CTA
   int* err;
 };
 
 // Launchers (adi_forward.cu).
-cudaError_t launch_x(const XArgs& a, int K, bool fp64, cudaStream_t st);
-cudaError_t launch_y(const YArgs& a, int K, bool fp64, cudaStream_t st);
+cudaError_t launch_x(const XArgs& a, int K, bool fp64, bool tree, cudaStream_t st);
+cudaError_t launch_y(const YArgs& a, int K, bool fp64, bool tree, cudaStream_t st);
 cudaError_t launch_gather(const GridDev* gd, const float* u_new, int ld, int n_rec, cudaStream_t st);
 cudaError_t launch_init(int nx, int ny, int ld, const float* m_pitched, const float* phi,
                         const float* psi, float* u0, float* u1, double tau, double cx_half,
@@ -64,8 +65,8 @@ cudaError_t launch_init(int nx, int ny, int ld, const float* m_pitched, const fl
                         const float* wavelet, int n_wavelet, cudaStream_t st);
 cudaError_t launch_scan_m(const float* m, int nx, int ny, int ld, unsigned int* out3,
                           cudaStream_t st);
-size_t x_smem_bytes(int spc, int tsys, bool fp64);
-size_t y_smem_bytes(int W, int C, int tcol, bool fp64);
+size_t x_smem_bytes(int spc, int tsys, bool fp64, bool tree);
+size_t y_smem_bytes(int W, int C, int tcol, bool fp64, bool tree);
 cudaError_t configure_kernels();
 
 }  // namespace adi

@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "adi_adjoint.h"
 #include "adi_internal.h"
 #include "adi_run.h"
 
@@ -40,6 +41,7 @@ int adi_wave::create(const adi_wave_desc* desc, int n, const float* const* m,
   if (n > 1) return fail(this, ADI_EUNSUPPORTED, "batched handles are created by adi_batch");
   if (!g_configured) {
     CK(configure_kernels(), "configure kernels");
+    CK(configure_adjoint_kernels(), "configure adjoint kernels");
     g_configured = true;
   }
   CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "create capture stream");
@@ -126,6 +128,7 @@ int adi_wave::start_grid(int s, const float* m, const float* phi, const float* p
   launches += 1;
   G.cur = 1;
   G.k = 1;
+  G.from_init = true;
   rr.valid = false;
   return ADI_OK;
 }
@@ -172,9 +175,25 @@ int adi_wave::prof_end(cudaStream_t st, cudaEvent_t a, int kind) {
 }
 
 int adi_wave::enqueue_step(Grid& G, cudaStream_t st, bool gather) {
-  const GridPlan& P = G.plan;
   float* u_cur = G.buf[G.cur];
   float* u_prev = G.buf[1 - G.cur];
+  int rc = launch_fwd(G, u_cur, u_prev, G.w, nullptr, G.gd, st);
+  if (rc != ADI_OK) return rc;
+  if (gather) {
+    CK(launch_gather(G.gd, u_prev, G.ld, G.hgd.n_rec, st), "gather launch");
+    launches += 1;
+  }
+  G.cur = 1 - G.cur;
+  G.k += 1;
+  G.from_init = false;
+  return ADI_OK;
+}
+
+// One forward step on explicit buffers: x sweep into w, y sweep + update
+// writing u^{k+1} over u_prev (and z into z_out when given).
+int adi_wave::launch_fwd(Grid& G, const float* u_cur, float* u_prev, float* w, float* z_out,
+                         GridDev* gd, cudaStream_t st) {
+  const GridPlan& P = G.plan;
   XArgs xa;
   xa.nx = G.nx;
   xa.ny = G.ny;
@@ -184,12 +203,12 @@ int adi_wave::enqueue_step(Grid& G, cudaStream_t st, bool gather) {
   xa.pcr = P.pcr;
   xa.m = G.m;
   xa.u = u_cur;
-  xa.w = G.w;
+  xa.w = w;
   xa.cx = G.dt * G.dt / (G.hx * G.hx);
   xa.cy = G.dt * G.dt / (G.hy * G.hy);
   xa.sc = G.dt * G.dt / (2.0 * G.hx * G.hx);
   xa.src_scale = G.dt * G.dt / (G.hx * G.hy);
-  xa.gd = G.gd;
+  xa.gd = gd;
   YArgs ya;
   ya.nx = G.nx;
   ya.ny = G.ny;
@@ -199,27 +218,22 @@ int adi_wave::enqueue_step(Grid& G, cudaStream_t st, bool gather) {
   ya.C = P.C;
   ya.pcr = P.pcr;
   ya.m = G.m;
-  ya.w = G.w;
+  ya.w = w;
   ya.u_cur = u_cur;
   ya.u_prev = u_prev;
+  ya.z_out = z_out;
   ya.sc = G.dt * G.dt / (2.0 * G.hy * G.hy);
-  ya.gd = G.gd;
+  ya.gd = gd;
   ya.err = d_err;
 
   cudaEvent_t a = nullptr;
   if (profile && prof_begin(st, &a) != ADI_OK) return ADI_ECUDA;
-  CK(launch_x(xa, P.kx, P.fp64x, st), "x sweep launch");
+  CK(launch_x(xa, P.kx, P.fp64x, P.tree, st), "x sweep launch");
   if (profile && prof_end(st, a, ADI_KERNEL_X) != ADI_OK) return ADI_ECUDA;
   if (profile && prof_begin(st, &a) != ADI_OK) return ADI_ECUDA;
-  CK(launch_y(ya, P.ky, P.fp64y, st), "y sweep launch");
+  CK(launch_y(ya, P.ky, P.fp64y, P.tree, st), "y sweep launch");
   if (profile && prof_end(st, a, ADI_KERNEL_Y) != ADI_OK) return ADI_ECUDA;
   launches += 2;
-  if (gather) {
-    CK(launch_gather(G.gd, u_prev, G.ld, G.hgd.n_rec, st), "gather launch");
-    launches += 1;
-  }
-  G.cur = 1 - G.cur;
-  G.k += 1;
   return ADI_OK;
 }
 
@@ -314,6 +328,7 @@ int adi_wave::run(int steps, const adi_source* src, const int32_t* rec_xy, int n
     rr.k0 = G.k;
     rr.steps = steps;
     rr.every = every;
+    rr.taylor = G.start == ADI_START_TAYLOR2 && G.from_init && G.k == 1;
     rr.src = sr;
     rr.rec.assign(rec_xy ? rec_xy : (const int32_t*)nullptr,
                   rec_xy ? rec_xy + 2 * (size_t)n_rec : (const int32_t*)nullptr);
@@ -379,6 +394,7 @@ int adi_wave::set_state(int shot, const float* u_prev, const float* u_cur, int64
   CK(cudaMemcpy2DAsync(G.buf[G.cur], sizeof(float) * G.ld, u_cur, wb, wb, G.ny,
                        cudaMemcpyDeviceToDevice, st), "set_state");
   G.k = k;
+  G.from_init = false;
   G.hgd.k = k;
   G.hgd.k0 = k;
   G.hgd.steps = 0;
@@ -444,6 +460,7 @@ adi_wave::~adi_wave() {
     cudaFree(G.gd);
   }
   for (float* p : rr.ckpt) cudaFree(p);
+  free_adj_work();
   for (const ProfRec& r : prof) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -455,8 +472,3 @@ adi_wave::~adi_wave() {
   if (cap) cudaStreamDestroy(cap);
 }
 
-int adi_wave::adjoint(const float* resid, double* grad_m, float* grad_wavelet, int every,
-                      cudaStream_t st) {
-  (void)resid; (void)grad_m; (void)grad_wavelet; (void)every; (void)st;
-  return fail(this, ADI_EUNSUPPORTED, "adjoint not built yet");
-}

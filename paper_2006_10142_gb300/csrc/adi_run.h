@@ -23,6 +23,7 @@ struct GridPlan {
   int ky = 8, log2W = 3, log2tcol = 0, C = 1;
   bool fp64y = false;
   int graph = 1;
+  bool tree = true;  // solver variant (see adi_sweeps.cuh)
 };
 
 struct Grid {
@@ -34,6 +35,7 @@ struct Grid {
   float* w = nullptr;               // scratch [ny][ld]
   int cur = 1;
   long long k = 1;
+  bool from_init = true;            // state is the start-up's (u^0, u^1), untouched since
   GridDev* gd = nullptr;            // device copy
   GridDev hgd = {};                 // host mirror
   double mmin = 0, mmax = 0;
@@ -50,11 +52,28 @@ struct RunRecord {
   std::vector<int> rec;             // [n_rec][2] host copy
   std::vector<float*> ckpt;         // checkpoint c: 2 fields (u^{k-1}, u^k) at step c*every
   size_t ckpt_bytes = 0;
+  bool taylor = false;              // run started at level 1 right after a Taylor start-up
 };
 
 struct ProfRec {
   cudaEvent_t a, b;
   int kind;
+};
+
+// Device workspace of adi_wave_adjoint (allocated on first use, reused).
+struct AdjWork {
+  size_t fbytes = 0;  // bytes of one pitched field
+  int E = 0;          // segment length it was sized for
+  float* wseg = nullptr;  // [E] forward x-sweep results of a segment
+  float* zseg = nullptr;  // [E] forward y-sweep results of a segment
+  float* wb = nullptr;    // wbar
+  float* rb = nullptr;    // rbar
+  float* L[3] = {nullptr, nullptr, nullptr};  // lam^{k+1}, lam^k, lam^{k-1}
+  float* A = nullptr;     // recompute state
+  float* B = nullptr;
+  GridDev* gd = nullptr;
+  int* rec = nullptr;
+  int rec_cap = 0;
 };
 
 }  // namespace adi
@@ -67,9 +86,10 @@ struct adi_wave {
   int rec_cap = 0;
   cudaStream_t cap = nullptr;  // private stream used only for graph capture
   cudaGraphExec_t pair[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [orientation][gather]
-  adi_wave_tuning tuning = {0, 0, 0, 0, 0, 0};
+  adi_wave_tuning tuning = {0, 0, 0, 0, 0, 0, 0};
   int ckpt_every = 0;
   adi::RunRecord rr;
+  adi::AdjWork aw;
   bool profile = false;
   std::vector<adi::ProfRec> prof;
   std::vector<cudaEvent_t> ev_pool;
@@ -93,6 +113,10 @@ struct adi_wave {
 
   // internals
   int enqueue_step(adi::Grid& G, cudaStream_t st, bool gather);
+  int launch_fwd(adi::Grid& G, const float* u_cur, float* u_prev, float* w, float* z_out,
+                 adi::GridDev* gd, cudaStream_t st);
+  int ensure_adj_work(adi::Grid& G, int E, int n_rec);
+  void free_adj_work();
   int launch_pair_graph(adi::Grid& G, cudaStream_t st, bool gather);
   void drop_graphs();
   int prof_begin(cudaStream_t st, cudaEvent_t* a);

@@ -1,0 +1,142 @@
+"""GPU adjoint (C ABI adi_wave_adjoint) against the FP64 oracle adjoint and
+against finite differences of the GPU forward run.
+
+Bars: gradient wrt m and wrt the wavelet within relative L2 1e-4 of the FP64
+oracle adjoint on 64x64 grids (same FP32 inputs and residuals); at 1024x1024,
+2000 steps (checkpoint every 50), the directional derivative matches central
+differences of the GPU misfit within 1e-2 in 16 seeded directions.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2006_10142_gb300 import inputs
+from helpers import THREADS, f32, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev():
+    import torch
+    return torch.device("cuda:0")
+
+
+def _setup(n=64, steps=150, seed=2, start="paper"):
+    prob, m_true = inputs.adjoint_problem(n, steps, seed=seed, n_rec=16)
+    return prob, m_true
+
+
+def _gpu_forward(prob, m, every, start="paper", phi=None):
+    import torch
+    from paper_2006_10142_gb300 import api
+    dev = _dev()
+    n = prob.n
+    wav = torch.from_numpy(f32(prob.wavelet)).to(dev)
+    phi_t = torch.from_numpy(f32(phi if phi is not None else np.zeros((n, n)))).to(dev)
+    h = api.AdiWave(torch.from_numpy(f32(m)).to(dev), phi_t, prob.tau, start=start,
+                    src=prob.src, wavelet=wav)
+    h.set_checkpointing(every)
+    tr = h.run(prob.steps, src=prob.src, wavelet=wav, rec=prob.rec)
+    return h, tr
+
+
+def _oracle_grad(prob, m, resid, start="paper", phi=None):
+    n = prob.n
+    hx = 1.0 / (n + 1)
+    m64 = f32(m).astype(np.float64)
+    phi64 = f32(phi if phi is not None else np.zeros((n, n))).astype(np.float64)
+    wav64 = f32(prob.wavelet).astype(np.float64)
+    u0, u1 = oracle.adi_init(m64, phi64, hx, hx, prob.tau, taylor=(start == "taylor2"),
+                             wv0=wav64[0], src=prob.src)
+    return oracle.adi_adjoint(m64, u0, u1, hx, hx, prob.tau, prob.steps,
+                              np.asarray(resid, dtype=np.float64), prob.rec, k0=1, src=prob.src,
+                              wavelet=wav64, taylor_k0=(start == "taylor2"), threads=THREADS)
+
+
+@pytest.mark.parametrize("every", [1, 7, 50, 150])
+def test_adjoint_matches_fp64_oracle(every):
+    import torch
+    prob, m_true = _setup()
+    # observed data from the perturbed medium (oracle, FP64)
+    n = prob.n
+    hx = 1.0 / (n + 1)
+    z = np.zeros((n, n))
+    _, _, d = oracle.adi_run(f32(m_true).astype(np.float64), z, z, hx, hx, prob.tau, prob.steps,
+                             src=prob.src, wavelet=f32(prob.wavelet).astype(np.float64),
+                             rec=prob.rec, threads=THREADS)
+    h, tr = _gpu_forward(prob, prob.m, every)
+    resid = (tr.double().cpu().numpy() - d).astype(np.float32)
+    gm, gw = h.adjoint(torch.from_numpy(resid).to(_dev()))
+    h.sync_status()
+    ref = _oracle_grad(prob, prob.m, resid)
+    e_m = rel_l2(gm.cpu().numpy(), ref["grad_m"])
+    e_w = rel_l2(gw.double().cpu().numpy(), ref["grad_wavelet"])
+    assert e_m < 1e-4 and e_w < 1e-4, (e_m, e_w)
+    h.close()
+
+
+def test_adjoint_taylor_start_and_initial_state():
+    import torch
+    prob, _ = _setup(n=48, steps=80)
+    phi = 0.01 * inputs.standing_wave(48, 48)
+    h, tr = _gpu_forward(prob, prob.m, 10, start="taylor2", phi=phi)
+    rng = np.random.default_rng(4)
+    resid = (1e-3 * rng.standard_normal(tr.shape)).astype(np.float32)
+    gm, gw = h.adjoint(torch.from_numpy(resid).to(_dev()))
+    ref = _oracle_grad(prob, prob.m, resid, start="taylor2", phi=phi)
+    assert rel_l2(gm.cpu().numpy(), ref["grad_m"]) < 1e-4
+    assert rel_l2(gw.double().cpu().numpy(), ref["grad_wavelet"]) < 1e-4
+    h.close()
+
+
+def test_adjoint_needs_checkpoints():
+    import torch
+    from paper_2006_10142_gb300 import api
+    prob, _ = _setup(n=32, steps=10)
+    h, tr = _gpu_forward(prob, prob.m, 0)
+    with pytest.raises(api.AdiError) as ei:
+        h.adjoint(torch.zeros_like(tr))
+    assert ei.value.code == 6
+    h.close()
+
+
+@pytest.mark.slow
+def test_adjoint_1024_finite_differences():
+    """The adjoint workload: 1024^2, 2000 steps, 64 receivers, checkpoint every 50."""
+    import torch
+    from paper_2006_10142_gb300 import api
+    prob, m_true = inputs.adjoint_problem(1024, 2000, seed=0, n_rec=64)
+    dev = _dev()
+    wav = torch.from_numpy(f32(prob.wavelet)).to(dev)
+    zeros = torch.zeros((1024, 1024), device=dev)
+
+    def traces(m):
+        h = api.AdiWave(torch.from_numpy(f32(m)).to(dev), zeros, prob.tau, src=prob.src,
+                        wavelet=wav)
+        tr = h.run(prob.steps, src=prob.src, wavelet=wav, rec=prob.rec)
+        h.sync_status()
+        out = tr.double().cpu().numpy()
+        h.close()
+        return out
+
+    d = traces(m_true)
+    h = api.AdiWave(torch.from_numpy(f32(prob.m)).to(dev), zeros, prob.tau, src=prob.src,
+                    wavelet=wav)
+    h.set_checkpointing(50)
+    tr = h.run(prob.steps, src=prob.src, wavelet=wav, rec=prob.rec)
+    resid = tr.double().cpu().numpy() - d
+    gm, _ = h.adjoint(torch.from_numpy(resid.astype(np.float32)).to(dev), ckpt_every=50)
+    h.sync_status()
+    g = gm.cpu().numpy()
+    J = lambda t: 0.5 * np.sum((t - d) ** 2)
+    errs = []
+    for q in range(16):
+        dm = inputs.smooth_direction(1024, q) * prob.m
+        eps = 1e-3 * np.linalg.norm(prob.m) / np.linalg.norm(dm)
+        fd = (J(traces(prob.m + eps * dm)) - J(traces(prob.m - eps * dm))) / (2 * eps)
+        an = float(np.sum(g * dm))
+        errs.append(abs(fd - an) / max(abs(fd), 1e-30))
+    assert max(errs) < 1e-2, errs
+    h.close()

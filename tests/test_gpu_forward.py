@@ -62,24 +62,27 @@ def test_ragged_grids_match_oracle(nx, ny):
     assert rel_l2(g["traces"], o["traces"]) < TOL
 
 
+@pytest.mark.parametrize("solver", [1, 2])
 @pytest.mark.parametrize("kx,ky,pcr,W", [(4, 4, 32, 8), (8, 8, 2, 16), (16, 16, 8, 32),
                                          (32, 32, 32, 8), (16, 4, 16, 4), (4, 32, 4, 32)])
-def test_tuning_variants_match_oracle(kx, ky, pcr, W):
+def test_tuning_variants_match_oracle(kx, ky, pcr, W, solver):
     nx, ny, steps = 300, 260, 8
     m, phi, tau, src, wav = _problem(nx, ny, steps, seed=7)
-    tun = dict(chunk_x=kx, chunk_y=ky, pcr_size=pcr, cols_per_cta=W)
+    tun = dict(chunk_x=kx, chunk_y=ky, pcr_size=pcr, cols_per_cta=W, solver=solver)
     g = gpu_run(m, phi, tau, steps, src=src, wavelet=wav, tuning=tun)
     o = oracle_run(m, phi, tau, steps, src=src, wavelet=wav)
     assert g["tuning"]["chunk_x"] == kx and g["tuning"]["chunk_y"] == ky
     assert rel_l2(g["u_cur"], o["u_cur"]) < TOL
 
 
-@pytest.mark.parametrize("ny,ky", [(4096, 4), (8191, 4), (3000, 8)])
-def test_cluster_y_sweep_matches_oracle(ny, ky):
+@pytest.mark.parametrize("ny,ky,solver", [(4096, 4, 2), (8191, 4, 2), (3000, 8, 2),
+                                          (4096, 8, 1), (8191, 16, 1), (3000, 8, 1),
+                                          (16384, 16, 1)])
+def test_cluster_y_sweep_matches_oracle(ny, ky, solver):
     """Columns long enough that the y sweep spans a thread-block cluster (DSMEM)."""
     nx, steps = 40, 6
     m, phi, tau, src, wav = _problem(nx, ny, steps, seed=3)
-    g = gpu_run(m, phi, tau, steps, src=src, wavelet=wav, tuning=dict(chunk_y=ky))
+    g = gpu_run(m, phi, tau, steps, src=src, wavelet=wav, tuning=dict(chunk_y=ky, solver=solver))
     o = oracle_run(m, phi, tau, steps, src=src, wavelet=wav)
     assert rel_l2(g["u_cur"], o["u_cur"]) < TOL
 
