@@ -242,8 +242,9 @@ size_t y_smem_bytes(int W, int C, int tcol, bool fp64, bool tree) {
   const size_t slots = (W + C - 1) / C;
   if (tree) {
     const int threads = W * tcol;
-    return fp64 ? YTreeSmem<double>::bytes(threads, (int)slots)
-                : YTreeSmem<float>::bytes(threads, (int)slots);
+    const int G = C * std::max(1, tcol / 32);
+    return fp64 ? YTreeSmem<double>::bytes(threads, (int)slots, G)
+                : YTreeSmem<float>::bytes(threads, (int)slots, G);
   }
   const size_t N = 2 * (size_t)C * tcol;
   return fp64 ? slots * N * (sizeof(Eq<double>) + sizeof(double))

@@ -47,19 +47,37 @@ __device__ __forceinline__ int ilog2_dev(int v) { return 31 - __clz(v); }
 // ---------------------------------------------------------------------------
 // shared-memory layouts
 // ---------------------------------------------------------------------------
+// Every region starts on a 64-byte boundary: Seg / Eq are stored with vector
+// instructions that need their natural (16- or 32-byte) alignment.
+__host__ __device__ constexpr size_t align64(size_t b) { return (b + 63) & ~size_t(63); }
+
 template <typename T> struct XTreeSmem {
-  // nodes[nwarps][31], tops[nwarps] (one summary per warp), xtop[nwarps][2]
+  // nodes[nwarps][31] | tops[nwarps] (one summary per warp) | xtop[nwarps][2]
+  static __host__ __device__ size_t off_tops(int nwarps) {
+    return align64((size_t)nwarps * 31 * sizeof(Node<T>));
+  }
+  static __host__ __device__ size_t off_xtop(int nwarps) {
+    return off_tops(nwarps) + align64((size_t)nwarps * sizeof(Seg<T>));
+  }
   static __host__ __device__ size_t bytes(int nwarps) {
-    return (size_t)nwarps * (31 * sizeof(Node<T>) + sizeof(Seg<T>) + 2 * sizeof(T));
+    return off_xtop(nwarps) + align64((size_t)nwarps * 2 * sizeof(T));
   }
 };
 
 template <typename T> struct YTreeSmem {
-  // csum[threads] (chunk summaries, later chunk end values), nodes[nwarps][31],
-  // tops[n_slots][32] (group summaries of owned columns), xtop[n_slots][32][2]
-  static __host__ __device__ size_t bytes(int threads, int n_slots) {
-    return (size_t)threads * sizeof(Seg<T>) + (size_t)(threads / 32) * 31 * sizeof(Node<T>) +
-           (size_t)n_slots * 32 * (sizeof(Seg<T>) + 2 * sizeof(T));
+  // csum[threads] (chunk summaries, later chunk end values) | nodes[nwarps][31]
+  // | tops[n_slots][G] (group summaries of owned columns) | xtop[n_slots][G][2]
+  static __host__ __device__ size_t off_nodes(int threads) {
+    return align64((size_t)threads * sizeof(Seg<T>));
+  }
+  static __host__ __device__ size_t off_tops(int threads) {
+    return off_nodes(threads) + align64((size_t)(threads / 32) * 31 * sizeof(Node<T>));
+  }
+  static __host__ __device__ size_t off_xtop(int threads, int n_slots, int G) {
+    return off_tops(threads) + align64((size_t)n_slots * G * sizeof(Seg<T>));
+  }
+  static __host__ __device__ size_t bytes(int threads, int n_slots, int G) {
+    return off_xtop(threads, n_slots, G) + align64((size_t)n_slots * G * 2 * sizeof(T));
   }
 };
 
@@ -87,8 +105,8 @@ __device__ __forceinline__ void x_solve_rows(unsigned char* smem, int spc, int l
       seg_solve_closed<T>(S, xa, xc);
     } else {
       const int nw = 1 << (log2tsys - 5);  // warps per row
-      Seg<T>* tops = reinterpret_cast<Seg<T>*>(reinterpret_cast<Node<T>*>(smem) + nwarps * 31);
-      T* xtop = reinterpret_cast<T*>(tops + nwarps);
+      Seg<T>* tops = reinterpret_cast<Seg<T>*>(smem + XTreeSmem<T>::off_tops(nwarps));
+      T* xtop = reinterpret_cast<T*>(smem + XTreeSmem<T>::off_xtop(nwarps));
       const int wis = p >> 5;
       if (lane == 0) tops[sys * nw + wis] = S;
       __syncthreads();
@@ -165,10 +183,14 @@ __device__ __forceinline__ void y_solve_cols(unsigned char* smem, int log2W, int
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const int threads = blockDim.x;
+    const int lg = log2tcol < 5 ? log2tcol : 5;  // tree levels
+    const int LG = 1 << lg;                       // lanes per group
+    const int gpc = tcol >> lg;                   // groups per column in this CTA
+    const int G = C * gpc;                        // groups per column over the cluster (<= 32)
     Seg<T>* csum = reinterpret_cast<Seg<T>*>(smem);
-    Node<T>* nodes = reinterpret_cast<Node<T>*>(csum + threads) + warp * 31;
-    Seg<T>* tops = reinterpret_cast<Seg<T>*>(reinterpret_cast<Node<T>*>(csum + threads) + nwarps * 31);
-    T* xtop = reinterpret_cast<T*>(tops + n_slots * 32);
+    Node<T>* nodes = reinterpret_cast<Node<T>*>(smem + YTreeSmem<T>::off_nodes(threads)) + warp * 31;
+    Seg<T>* tops = reinterpret_cast<Seg<T>*>(smem + YTreeSmem<T>::off_tops(threads));
+    T* xtop = reinterpret_cast<T*>(smem + YTreeSmem<T>::off_xtop(threads, n_slots, G));
     const int q = gq - rank * tcol;
     {
       Seg<T> S;
@@ -177,19 +199,15 @@ __device__ __forceinline__ void y_solve_cols(unsigned char* smem, int log2W, int
     }
     __syncthreads();
     // re-map: each warp reduces up to 32 consecutive chunks of one column
-    const int lg = log2tcol < 5 ? log2tcol : 5;  // tree levels
-    const int LG = 1 << lg;                       // lanes per group
-    const int gpc = tcol >> lg;                   // groups per column in this CTA
     const int task = warp * (32 >> lg) + (lane >> lg);  // (column, group) handled by this lane
     const int tc = task / gpc;
     const int tg = task % gpc;
     const int chunk = tg * LG + (lane & (LG - 1));
     Seg<T> S = csum[tc * tcol + chunk];
     S = warp_tree_up<T>(S, nodes, lane, lg);
-    const int G = C * gpc;          // groups per column over the whole cluster (<= 32)
     const int gg = rank * gpc + tg;  // global group index of this lane's group
     const int t_owner = tc % C, t_slot = tc / C;
-    Seg<T>* tdst = tops + t_slot * 32 + gg;
+    Seg<T>* tdst = tops + t_slot * G + gg;
     if (C > 1) {
       cgx::cluster_group cl = cgx::this_cluster();
       cluster_wait_started(C);
@@ -202,27 +220,27 @@ __device__ __forceinline__ void y_solve_cols(unsigned char* smem, int log2W, int
     for (int sl = warp; sl < n_own; sl += nwarps) {
       Eq<T> E0 = eq_identity<T>(), E1 = eq_identity<T>();
       if (lane < G) {
-        E0 = tops[sl * 32 + lane].f;
-        E1 = tops[sl * 32 + lane].l;
+        E0 = tops[sl * G + lane].f;
+        E1 = tops[sl * G + lane].l;
       }
       pcr64<T>(E0, E1, lane, 2 * G);
       if (lane < G) {
-        xtop[2 * (sl * 32 + lane)] = div_t(E0.d, E0.b);
-        xtop[2 * (sl * 32 + lane) + 1] = div_t(E1.d, E1.b);
+        xtop[2 * (sl * G + lane)] = div_t(E0.d, E0.b);
+        xtop[2 * (sl * G + lane) + 1] = div_t(E1.d, E1.b);
       }
     }
     T xa, xc;
     if (C > 1) {
       cgx::cluster_group cl = cgx::this_cluster();
       cl.sync();
-      const T* src = cl.map_shared_rank(xtop + 2 * (t_slot * 32 + gg), t_owner);
+      const T* src = cl.map_shared_rank(xtop + 2 * (t_slot * G + gg), t_owner);
       xa = src[0];
       xc = src[1];
       cl.sync();  // owners keep their shared memory until every read is done
     } else {
       __syncthreads();
-      xa = xtop[2 * (t_slot * 32 + gg)];
-      xc = xtop[2 * (t_slot * 32 + gg) + 1];
+      xa = xtop[2 * (t_slot * G + gg)];
+      xc = xtop[2 * (t_slot * G + gg) + 1];
     }
     warp_tree_down<T>(nodes, lane, lg, xa, xc);
     // hand the chunk end values back to the threads that own the chunks
