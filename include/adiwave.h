@@ -196,7 +196,9 @@ const char *adi_wave_last_error(const adi_wave *h);
  *                   system across warp lanes by register shuffles, PCR of the
  *                   warp summaries) or ADI_SOLVER_CR_SMEM (cyclic reduction
  *                   level by level in shared memory, PCR for the last
- *                   `pcr_size` equations).
+ *                   `pcr_size` equations);
+ * cta_threads:      upper bound on threads per CTA in both sweeps (64, 128,
+ *                   256, 512 or 1024; smaller CTAs let two share an SM).
  * Zero fields mean "choose automatically". */
 enum { ADI_SOLVER_AUTO = 0, ADI_SOLVER_TREE = 1, ADI_SOLVER_CR_SMEM = 2 };
 typedef struct {
@@ -206,6 +208,7 @@ typedef struct {
     int32_t pcr_size;
     int32_t use_graph;
     int32_t solver;
+    int32_t cta_threads;
 } adi_wave_tuning;
 
 int adi_wave_get_tuning(const adi_wave *h, adi_wave_tuning *t);
@@ -222,6 +225,22 @@ enum { ADI_KERNEL_X = 0, ADI_KERNEL_Y = 1, ADI_KERNEL_OTHER = 2, ADI_KERNEL_KIND
 int adi_wave_profile(adi_wave *h, int32_t enable);
 int adi_wave_profile_read(adi_wave *h, double *ms, int64_t *launches,
                           int32_t n_kinds);
+
+/* ---- batched form (n_shots > 1) -------------------------------------------
+ * mode 0 (default): every step of all shots is one persistent kernel launch
+ * that hands out x-sweep and y-sweep work items of all shots from a global
+ * queue (y items of a shot wait, bounded, for that shot's x items);
+ * mode 1: the plain x and y kernels launched once per shot and step (the
+ * comparison point).  ADI_EINVAL for other modes or single-grid handles. */
+int adi_wave_set_batch_mode(adi_wave *h, int32_t mode);
+
+/* Failure-detection hook of the batched kernel.  spin_limit bounds the
+ * dependency wait of a y item (iterations of ~0.25 us; 0 restores the
+ * default, about one second); never_ready_shot >= 0 makes that shot's wait
+ * target unreachable, so its y items time out: the kernel still finishes,
+ * skips those items and adi_wave_sync_status() returns ADI_ETIMEOUT.  -1
+ * disables it. */
+int adi_wave_set_wait_hook(adi_wave *h, int64_t spin_limit, int32_t never_ready_shot);
 
 /* Number of kernel launches the handle has enqueued since creation (all
  * kinds, graph replays counted per kernel node). */

@@ -41,7 +41,7 @@ EXPORTS = (
     "adi_wave_adjoint", "adi_wave_get_state", "adi_wave_set_state", "adi_wave_sync_status",
     "adi_wave_destroy", "adi_wave_strerror", "adi_wave_last_error", "adi_wave_get_tuning",
     "adi_wave_set_tuning", "adi_wave_profile", "adi_wave_profile_read", "adi_wave_launch_count",
-    "adi_wave_version",
+    "adi_wave_version", "adi_wave_set_batch_mode", "adi_wave_set_wait_hook",
 )
 
 
@@ -60,7 +60,7 @@ class Tuning(ctypes.Structure):
     _fields_ = [("chunk_x", ctypes.c_int32), ("chunk_y", ctypes.c_int32),
                 ("rows_per_cta", ctypes.c_int32), ("cols_per_cta", ctypes.c_int32),
                 ("pcr_size", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("solver", ctypes.c_int32)]
+                ("solver", ctypes.c_int32), ("cta_threads", ctypes.c_int32)]
 
 
 class AdiError(RuntimeError):
@@ -118,6 +118,8 @@ def load(build_if_missing: bool = True):
         lib.adi_wave_launch_count.restype = i64
         lib.adi_wave_version.argtypes = []
         lib.adi_wave_version.restype = ctypes.c_char_p
+        lib.adi_wave_set_batch_mode.argtypes = [P, i32]
+        lib.adi_wave_set_wait_hook.argtypes = [P, i64, i32]
         for name in EXPORTS:
             if not hasattr(lib, name):
                 raise RuntimeError("libadiwave.so does not export %s" % name)

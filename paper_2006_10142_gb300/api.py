@@ -199,5 +199,102 @@ class AdiWave:
         return int(self._lib.adi_wave_launch_count(self._h))
 
 
+class AdiWaveBatch:
+    """Many independent grids ("shots") of uneven size advanced together.
+
+    ``ms``, ``phis`` (and optional ``psis``): lists of float32 CUDA tensors
+    [ny_b, nx_b]; ``dts``: tau per shot (a float applies to all).  Each step of
+    all shots is one persistent kernel launch (``mode=0``) or the plain
+    kernels launched per shot (``mode=1``).
+    """
+
+    def __init__(self, ms: Sequence[torch.Tensor], phis: Sequence[torch.Tensor], dts,
+                 psis=None, start: str = "paper", fp64: str = "auto", stream=None):
+        self._lib = _lib.load()
+        n = len(ms)
+        if n < 2 or len(phis) != n:
+            raise ValueError("a batch needs >= 2 shots and one phi per m")
+        if not isinstance(dts, (list, tuple)):
+            dts = [dts] * n
+        self.shapes = []
+        keep = []
+        descs = (Desc * n)()
+        mp = (ctypes.c_void_p * n)()
+        pp = (ctypes.c_void_p * n)()
+        sp = (ctypes.c_void_p * n)()
+        for b in range(n):
+            ny, nx = phis[b].shape
+            m = _dev_f32(ms[b], "m[%d]" % b, (ny, nx))
+            phi = _dev_f32(phis[b], "phi[%d]" % b, (ny, nx))
+            psi = _dev_f32(psis[b], "psi[%d]" % b, (ny, nx)) if psis and psis[b] is not None else None
+            keep += [m, phi, psi]
+            descs[b] = Desc(int(nx), int(ny), 1.0, 1.0, float(dts[b]), _START[start], _FP64[fp64])
+            mp[b], pp[b] = m.data_ptr(), phi.data_ptr()
+            sp[b] = psi.data_ptr() if psi is not None else 0
+            self.shapes.append((int(ny), int(nx)))
+        self.device = phis[0].device
+        self._keep = keep
+        h = ctypes.c_void_p()
+        rc = self._lib.adi_wave_init(ctypes.byref(h), descs, n, mp, pp, sp, None, _stream_ptr(stream))
+        _lib.check(rc, None, "adi_wave_init (batch)")
+        self._h = h
+        self.n = n
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.adi_wave_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_mode(self, mode: int):
+        _lib.check(self._lib.adi_wave_set_batch_mode(self._h, int(mode)), self._h, "set_batch_mode")
+
+    def set_wait_hook(self, spin_limit: int = 0, never_ready_shot: int = -1):
+        _lib.check(self._lib.adi_wave_set_wait_hook(self._h, int(spin_limit), int(never_ready_shot)),
+                   self._h, "set_wait_hook")
+
+    def run(self, steps: int, srcs=None, wavelets=None, stream=None):
+        """srcs: list of (ix, iy) or None per shot; wavelets: list of device tensors."""
+        arr = None
+        if srcs is not None:
+            arr = (Source * self.n)()
+            self._wav_keep = []
+            for b in range(self.n):
+                if srcs[b] is None:
+                    arr[b] = Source(-1, -1, None, 0)
+                else:
+                    w = _dev_f32(wavelets[b].reshape(-1), "wavelet[%d]" % b)
+                    self._wav_keep.append(w)
+                    arr[b] = Source(int(srcs[b][0]), int(srcs[b][1]), w.data_ptr(), int(w.numel()))
+        rc = self._lib.adi_wave_run(self._h, int(steps), arr, None, 0, ctypes.c_void_p(0),
+                                    _stream_ptr(stream))
+        _lib.check(rc, self._h, "run (batch)")
+
+    def state(self, shot: int, stream=None):
+        ny, nx = self.shapes[shot]
+        up = torch.empty((ny, nx), dtype=torch.float32, device=self.device)
+        uc = torch.empty_like(up)
+        k = ctypes.c_int64()
+        rc = self._lib.adi_wave_get_state(self._h, int(shot), _ptr(up), _ptr(uc), ctypes.byref(k),
+                                          _stream_ptr(stream))
+        _lib.check(rc, self._h, "get_state")
+        return up, uc, int(k.value)
+
+    def sync_status(self, stream=None):
+        _lib.check(self._lib.adi_wave_sync_status(self._h, _stream_ptr(stream)), self._h,
+                   "sync_status")
+
+    def profile(self, enable: bool = True):
+        _lib.check(self._lib.adi_wave_profile(self._h, int(bool(enable))), self._h)
+
+    def launch_count(self) -> int:
+        return int(self._lib.adi_wave_launch_count(self._h))
+
+
 def version() -> str:
     return _lib.load().adi_wave_version().decode()

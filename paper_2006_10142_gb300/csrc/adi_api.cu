@@ -21,6 +21,7 @@
 #include "../../include/adiwave.h"
 #include "adi_internal.h"
 #include "adi_run.h"
+#include "adi_sweeps.cuh"
 
 using namespace adi;
 
@@ -65,9 +66,11 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
   if (pcr != 2 && pcr != 4 && pcr != 8 && pcr != 16 && pcr != 32) { why = "pcr_size must be 2..32, a power of two"; return ADI_EINVAL; }
   P.pcr = pcr;
 
+  const int ct = t.cta_threads;
+  if (ct != 0 && ct != 64 && ct != 128 && ct != 256 && ct != 512 && ct != 1024) { why = "cta_threads must be 64..1024, a power of two"; return ADI_EINVAL; }
   // ---- x sweep
   {
-    const int maxT = P.fp64x ? 512 : 1024;
+    const int maxT = std::min(P.fp64x ? 512 : 1024, ct ? ct : 1024);
     int K = t.chunk_x;
     if (K == 0) K = P.fp64x ? 8 : (G.nx >= 512 ? 16 : (G.nx >= 64 ? 8 : 4));
     if (K != 4 && K != 8 && K != 16 && K != 32) { why = "chunk_x must be 4, 8, 16 or 32"; return ADI_EINVAL; }
@@ -83,14 +86,14 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
       spc = (spc + q - 1) / q * q;
       if (spc * tsys > maxT) spc = maxT / tsys;
     }
-    if (x_smem_bytes(spc, tsys, P.fp64x, P.tree) > 200 * 1024) { why = "x sweep shared memory too large"; return ADI_EUNSUPPORTED; }
+    if (x_smem_bytes(spc, tsys, P.fp64x, P.tree) > (size_t)kMaxDynSmem) { why = "x sweep shared memory too large"; return ADI_EUNSUPPORTED; }
     P.kx = K;
     P.log2tsys = ilog2(tsys);
     P.spc = spc;
   }
   // ---- y sweep
   {
-    const int maxT = P.fp64y ? 512 : 1024;
+    const int maxT = std::min(P.fp64y ? 512 : 1024, ct ? ct : 1024);
     const int maxC = 16;
     int W = t.cols_per_cta ? t.cols_per_cta : 8;
     if (W != 4 && W != 8 && W != 16 && W != 32) { why = "cols_per_cta must be 4, 8, 16 or 32"; return ADI_EINVAL; }
@@ -122,13 +125,15 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
     int tcol, C;
     geom(K, tcol, C);
     if (!fits(K)) { why = "ny too large for this chunk_y (cluster or top system)"; return ADI_EUNSUPPORTED; }
-    if (y_smem_bytes(W, C, tcol, P.fp64y, P.tree) > 200 * 1024) { why = "y sweep shared memory too large"; return ADI_EUNSUPPORTED; }
+    if (align64(y_smem_bytes(W, C, tcol, P.fp64y, P.tree)) + y_stage_bytes(W * tcol, K) >
+        (size_t)kMaxDynSmem) { why = "y sweep shared memory too large"; return ADI_EUNSUPPORTED; }
     P.ky = K;
     P.log2W = ilog2(W);
     P.log2tcol = ilog2(tcol);
     P.C = C;
   }
   P.graph = (t.use_graph >= 0) ? 1 : 0;
+  P.cta_threads = ct;
   G.plan = P;
   return ADI_OK;
 }
@@ -258,6 +263,7 @@ extern "C" int adi_wave_get_tuning(const adi_wave* h, adi_wave_tuning* t) {
   t->pcr_size = P.pcr;
   t->use_graph = P.graph ? 1 : -1;
   t->solver = P.tree ? ADI_SOLVER_TREE : ADI_SOLVER_CR_SMEM;
+  t->cta_threads = P.cta_threads;
   return ADI_OK;
 }
 
@@ -278,3 +284,19 @@ extern "C" int adi_wave_profile_read(adi_wave* h, double* ms, int64_t* launches,
 }
 
 extern "C" int64_t adi_wave_launch_count(const adi_wave* h) { return h ? h->launches : 0; }
+
+extern "C" int adi_wave_set_batch_mode(adi_wave* h, int32_t mode) {
+  if (!h || h->g.size() < 2 || (mode != 0 && mode != 1)) return ADI_EINVAL;
+  h->batch_mode = mode;
+  h->drop_graphs();
+  return ADI_OK;
+}
+
+extern "C" int adi_wave_set_wait_hook(adi_wave* h, int64_t spin_limit, int32_t never_ready_shot) {
+  if (!h || spin_limit < 0 || never_ready_shot < -1 || never_ready_shot >= (int)h->g.size())
+    return ADI_EINVAL;
+  h->spin_limit = spin_limit > 0 ? spin_limit : (1ll << 22);
+  h->never_ready = never_ready_shot;
+  h->drop_graphs();
+  return ADI_OK;
+}

@@ -1,0 +1,164 @@
+// adi_bodies.cuh -- one CTA's share of a forward step, shared by the plain
+// kernels (adi_forward.cu: one launch per sweep) and the persistent batched
+// kernel (adi_batch.cu: many grids, one launch per step).
+//
+//   x_rows_body : RHS assembly r = tau^2 (m Lap u^k + f^k) (Eq. CN1 in delta
+//                 form) fused with the row solves X w = r (Eq. fr1's
+//                 operator) for one block of rows;
+//   y_strip_body: the column solves Y z = w (Eq. fr2's operator) for one strip
+//                 of columns fused with u^{k+1} = 2u^k - u^{k-1} + z, written
+//                 over u^{k-1} (Algorithm 1's buffer swap).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "adi_device.cuh"
+#include "adi_internal.h"
+#include "adi_sweeps.cuh"
+
+namespace adi {
+
+// Rows blk*spc .. blk*spc+spc-1; 2^log2tsys threads per row, K contiguous
+// unknowns per thread.
+template <int K, typename T, bool TREE>
+__device__ __forceinline__ void x_rows_body(const XArgs& a, int blk, unsigned char* smem) {
+  const int tsys = 1 << a.log2tsys;
+  const int tid = threadIdx.x;
+  const int sys = tid >> a.log2tsys;
+  const int p = tid & (tsys - 1);
+  const int j = blk * a.spc + sys;
+  const int i0 = p * K;
+  const bool active = (j < a.ny) && (i0 < a.nx);
+  const size_t row = (size_t)j * a.ld;
+
+  T d[K], s[K];
+  if (active) {
+    const T cx = (T)a.cx, cy = (T)a.cy, sc = (T)a.sc;
+    float uc[K], v[K];
+    // vertical neighbours first, accumulated into d (halo rows j-1, j+1)
+    if (j > 0) {
+      load_vec<K>(v, a.u + row - a.ld + i0);
+#pragma unroll
+      for (int k = 0; k < K; ++k) d[k] = (T)v[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < K; ++k) d[k] = T(0);
+    }
+    if (j + 1 < a.ny) {
+      load_vec<K>(v, a.u + row + a.ld + i0);
+#pragma unroll
+      for (int k = 0; k < K; ++k) d[k] += (T)v[k];
+    }
+    load_vec<K>(uc, a.u + row + i0);
+    load_vec<K>(v, a.m + row + i0);
+    const float uL = (i0 > 0) ? __ldg(a.u + row + i0 - 1) : 0.f;
+    const float uR = (i0 + K < a.nx) ? __ldg(a.u + row + i0 + K) : 0.f;
+    // padding columns (i >= nx) hold zero u and zero m, so r = s = 0 there
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const T c = (T)uc[k];
+      const T l = (T)(k > 0 ? uc[k - 1] : uL);
+      const T r = (T)(k < K - 1 ? uc[k + 1] : uR);
+      const T lap = cx * (l + r - T(2) * c) + cy * (d[k] - T(2) * c);
+      d[k] = (T)v[k] * lap;
+      s[k] = sc * (T)v[k];
+    }
+    // point source f^k = w(t_k) / (h1 h2) at one node
+    const GridDev* gd = a.gd;
+    const int sx = gd->src_ix;
+    if (j == gd->src_iy && sx >= i0 && sx < i0 + K) {
+      const long long lev = gd->k;
+      if (gd->wavelet != nullptr && lev >= 0 && lev < gd->n_wavelet) {
+        const T f = (T)a.src_scale * (T)gd->wavelet[lev];
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          if (i0 + k == sx) d[k] += f;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < K; ++k) { d[k] = T(0); s[k] = T(0); }
+  }
+
+  x_solve_rows<K, T, TREE>(smem, a.spc, a.log2tsys, a.pcr, sys, p, d, s);
+  if (active) store_vec<K, T>(a.w + row + i0, d);
+}
+
+// Strip `strip` of 2^log2W columns, cluster rank `rank` of C along the
+// column (C = 1 outside clusters).  `bump` advances the grid's level k (one
+// CTA per grid and step does it).  A kernel with C > 1 must have executed
+// cluster_arrive_early() first.
+template <int K, typename T, bool TREE>
+__device__ __forceinline__ void y_strip_body(const YArgs& a, int strip, int rank, bool bump,
+                                             unsigned char* smem) {
+  const int W = 1 << a.log2W;
+  const int tcol = 1 << a.log2tcol;
+  const int C = a.C;
+  const int tid = threadIdx.x;
+  const int col = tid & (W - 1);
+  const int q = tid >> a.log2W;
+  const int gq = rank * tcol + q;
+  const int i = strip * W + col;
+  const int j0 = gq * K;
+  const bool colok = i < a.nx;
+  const bool full = colok && (j0 + K <= a.ny);
+  const size_t ld = (size_t)a.ld;
+  const size_t base = (size_t)j0 * ld + i;
+  const T sc = (T)a.sc;
+
+  // Stage u^k and u^{k-1} of this thread's rows into shared memory with
+  // asynchronous copies issued now, so that their HBM traffic overlaps the
+  // solve; the epilogue reads them back.  Layout [2][K][threads].
+  const int threads = blockDim.x;
+  float* stage = reinterpret_cast<float*>(smem + a.stage_off);
+  {
+    const uint32_t sb = (uint32_t)__cvta_generic_to_shared(stage + tid);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const bool ok = colok && (j0 + k) < a.ny;
+      const float* gc = ok ? a.u_cur + base + k * ld : a.u_cur;
+      const float* gp = ok ? a.u_prev + base + k * ld : a.u_prev;
+      const int nbytes = ok ? 4 : 0;  // 0: zero-fill without reading
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sb + 4u * (k * threads)),
+                   "l"(gc), "r"(nbytes) : "memory");
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;"
+                   ::"r"(sb + 4u * ((K + k) * threads)), "l"(gp), "r"(nbytes) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+
+  T d[K], s[K];
+  if (full) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      d[k] = (T)__ldcg(a.w + base + k * ld);
+      s[k] = sc * (T)__ldg(a.m + base + k * ld);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const bool ok = colok && (j0 + k) < a.ny;
+      d[k] = ok ? (T)__ldcg(a.w + base + k * ld) : T(0);
+      s[k] = ok ? sc * (T)__ldg(a.m + base + k * ld) : T(0);
+    }
+  }
+  y_solve_cols<K, T, TREE>(smem, a.log2W, a.log2tcol, C, rank, a.pcr, col, gq, d, s);
+
+  asm volatile("cp.async.wait_all;" ::: "memory");  // this thread's staged rows
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (full || (colok && (j0 + k) < a.ny)) {
+      const size_t idx = base + k * ld;
+      const float un = 2.0f * stage[k * threads + tid] - stage[(K + k) * threads + tid] + (float)d[k];
+      a.u_prev[idx] = un;
+      if (a.z_out) a.z_out[idx] = (float)d[k];
+      bad |= !isfinite(un);
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0 && a.err) atomicOr(a.err, ERR_NUMERIC);
+  if (bump && tid == 0 && a.gd) a.gd->k += 1;
+}
+
+}  // namespace adi

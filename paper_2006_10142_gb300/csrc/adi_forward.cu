@@ -14,6 +14,7 @@
 
 #include <algorithm>
 
+#include "adi_bodies.cuh"
 #include "adi_device.cuh"
 #include "adi_internal.h"
 #include "adi_sweeps.cuh"
@@ -21,141 +22,23 @@
 namespace adi {
 
 // ---------------------------------------------------------------------------
-// pass 1: RHS assembly + x solve.  CTA = `spc` rows, 2^log2tsys threads per
-// row, K contiguous unknowns per thread.
+// pass 1: RHS assembly + x solve (adi_bodies.cuh).  CTA = `spc` rows.
 // ---------------------------------------------------------------------------
 template <int K, typename T, int MAXT, bool TREE>
 __global__ void __launch_bounds__(MAXT, 1) x_sweep_kernel(const XArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int tsys = 1 << a.log2tsys;
-  const int tid = threadIdx.x;
-  const int sys = tid >> a.log2tsys;
-  const int p = tid & (tsys - 1);
-  const int j = blockIdx.x * a.spc + sys;
-  const int i0 = p * K;
-  const bool active = (j < a.ny) && (i0 < a.nx);
-  const size_t row = (size_t)j * a.ld;
-
-  T d[K], s[K];
-  if (active) {
-    const T cx = (T)a.cx, cy = (T)a.cy, sc = (T)a.sc;
-    float uc[K], v[K];
-    // vertical neighbours first, accumulated into d (halo rows j-1, j+1)
-    if (j > 0) {
-      load_vec<K>(v, a.u + row - a.ld + i0);
-#pragma unroll
-      for (int k = 0; k < K; ++k) d[k] = (T)v[k];
-    } else {
-#pragma unroll
-      for (int k = 0; k < K; ++k) d[k] = T(0);
-    }
-    if (j + 1 < a.ny) {
-      load_vec<K>(v, a.u + row + a.ld + i0);
-#pragma unroll
-      for (int k = 0; k < K; ++k) d[k] += (T)v[k];
-    }
-    load_vec<K>(uc, a.u + row + i0);
-    load_vec<K>(v, a.m + row + i0);
-    const float uL = (i0 > 0) ? __ldg(a.u + row + i0 - 1) : 0.f;
-    const float uR = (i0 + K < a.nx) ? __ldg(a.u + row + i0 + K) : 0.f;
-    // padding columns (i >= nx) hold zero u and zero m, so r = s = 0 there
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const T c = (T)uc[k];
-      const T l = (T)(k > 0 ? uc[k - 1] : uL);
-      const T r = (T)(k < K - 1 ? uc[k + 1] : uR);
-      const T lap = cx * (l + r - T(2) * c) + cy * (d[k] - T(2) * c);
-      d[k] = (T)v[k] * lap;
-      s[k] = sc * (T)v[k];
-    }
-    // point source f^k = w(t_k) / (h1 h2) at one node
-    const GridDev* gd = a.gd;
-    const int sx = gd->src_ix;
-    if (j == gd->src_iy && sx >= i0 && sx < i0 + K) {
-      const long long lev = gd->k;
-      if (gd->wavelet != nullptr && lev >= 0 && lev < gd->n_wavelet) {
-        const T f = (T)a.src_scale * (T)gd->wavelet[lev];
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-          if (i0 + k == sx) d[k] += f;
-      }
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < K; ++k) { d[k] = T(0); s[k] = T(0); }
-  }
-
-  x_solve_rows<K, T, TREE>(smem, a.spc, a.log2tsys, a.pcr, sys, p, d, s);
-  if (active) store_vec<K, T>(a.w + row + i0, d);
+  x_rows_body<K, T, TREE>(a, blockIdx.x, smem);
 }
 
 // ---------------------------------------------------------------------------
-// pass 2: y solve + update.  A strip of 2^log2W columns; a cluster of C CTAs
-// covers the whole column length, each CTA 2^log2tcol threads per column
-// with K consecutive rows per thread.
+// pass 2: y solve + update (adi_bodies.cuh).  A strip of 2^log2W columns; a
+// cluster of C CTAs covers the whole column length.
 // ---------------------------------------------------------------------------
 template <int K, typename T, int MAXT, bool TREE>
 __global__ void __launch_bounds__(MAXT, 1) y_sweep_kernel(const YArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int W = 1 << a.log2W;
-  const int tcol = 1 << a.log2tcol;
-  const int C = a.C;
-  cluster_arrive_early(C);
-  const int tid = threadIdx.x;
-  const int col = tid & (W - 1);
-  const int q = tid >> a.log2W;
-  const int rank = cluster_rank(C);
-  const int strip = blockIdx.x / C;
-  const int gq = rank * tcol + q;
-  const int i = strip * W + col;
-  const int j0 = gq * K;
-  const bool colok = i < a.nx;
-  const bool full = colok && (j0 + K <= a.ny);
-  const size_t ld = (size_t)a.ld;
-  const size_t base = (size_t)j0 * ld + i;
-  const T sc = (T)a.sc;
-
-  T d[K], s[K];
-  if (full) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      d[k] = (T)__ldg(a.w + base + k * ld);
-      s[k] = sc * (T)__ldg(a.m + base + k * ld);
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const bool ok = colok && (j0 + k) < a.ny;
-      d[k] = ok ? (T)__ldg(a.w + base + k * ld) : T(0);
-      s[k] = ok ? sc * (T)__ldg(a.m + base + k * ld) : T(0);
-    }
-  }
-  y_solve_cols<K, T, TREE>(smem, a.log2W, a.log2tcol, C, rank, a.pcr, col, gq, d, s);
-
-  bool bad = false;
-  if (full) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const size_t idx = base + k * ld;
-      const float un = 2.0f * __ldg(a.u_cur + idx) - a.u_prev[idx] + (float)d[k];
-      a.u_prev[idx] = un;
-      if (a.z_out) a.z_out[idx] = (float)d[k];
-      bad |= !isfinite(un);
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      if (colok && (j0 + k) < a.ny) {
-        const size_t idx = base + k * ld;
-        const float un = 2.0f * __ldg(a.u_cur + idx) - a.u_prev[idx] + (float)d[k];
-        a.u_prev[idx] = un;
-        if (a.z_out) a.z_out[idx] = (float)d[k];
-        bad |= !isfinite(un);
-      }
-    }
-  }
-  if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0 && a.err) atomicOr(a.err, ERR_NUMERIC);
-  if (blockIdx.x == 0 && tid == 0 && a.gd) a.gd->k += 1;
+  cluster_arrive_early(a.C);
+  y_strip_body<K, T, TREE>(a, blockIdx.x / a.C, cluster_rank(a.C), blockIdx.x == 0, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -251,6 +134,8 @@ size_t y_smem_bytes(int W, int C, int tcol, bool fp64, bool tree) {
               : slots * N * (sizeof(Eq<float>) + sizeof(float));
 }
 
+size_t y_stage_bytes(int threads, int K) { return align64((size_t)2 * K * threads * sizeof(float)); }
+
 template <int K, typename T, int MAXT, bool TREE>
 static cudaError_t launch_x_t(const XArgs& a, cudaStream_t st) {
   const int threads = a.spc << a.log2tsys;
@@ -262,15 +147,17 @@ static cudaError_t launch_x_t(const XArgs& a, cudaStream_t st) {
 }
 
 template <int K, typename T, int MAXT, bool TREE>
-static cudaError_t launch_y_t(const YArgs& a, cudaStream_t st) {
+static cudaError_t launch_y_t(const YArgs& a_in, cudaStream_t st) {
+  YArgs a = a_in;
   const int W = 1 << a.log2W;
   const int threads = W << a.log2tcol;
   if (threads % 32 != 0 || threads > MAXT) return cudaErrorInvalidValue;  // whole warps only
   const int strips = (a.nx + W - 1) / W;
+  a.stage_off = (int)align64(y_smem_bytes(W, a.C, 1 << a.log2tcol, sizeof(T) == 8, TREE));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(strips * a.C, 1, 1);
   cfg.blockDim = dim3(threads, 1, 1);
-  cfg.dynamicSmemBytes = y_smem_bytes(W, a.C, 1 << a.log2tcol, sizeof(T) == 8, TREE);
+  cfg.dynamicSmemBytes = a.stage_off + y_stage_bytes(threads, K);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -315,7 +202,7 @@ cudaError_t launch_y(const YArgs& a, int K, bool fp64, bool tree, cudaStream_t s
 template <typename KernT>
 static cudaError_t allow_smem(KernT kern, bool cluster16) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       200 * 1024);
+                                       kMaxDynSmem);
   if (e != cudaSuccess) return e;
   if (cluster16) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   return e;

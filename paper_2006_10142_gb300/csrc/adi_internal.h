@@ -53,6 +53,7 @@ struct YArgs {
   double sc;           // tau^2 / (2 h2^2)
   GridDev* gd;         // k is advanced by one CTA
   int* err;
+  int stage_off;       // byte offset of the u^k / u^{k-1} staging area in shared memory
 };
 
 // Launchers (adi_forward.cu).
@@ -67,6 +68,8 @@ cudaError_t launch_scan_m(const float* m, int nx, int ny, int ld, unsigned int* 
                           cudaStream_t st);
 size_t x_smem_bytes(int spc, int tsys, bool fp64, bool tree);
 size_t y_smem_bytes(int W, int C, int tcol, bool fp64, bool tree);
+size_t y_stage_bytes(int threads, int K);
+constexpr int kMaxDynSmem = 227 * 1024;
 cudaError_t configure_kernels();
 
 }  // namespace adi

@@ -38,7 +38,6 @@ int adi_wave::upload_gd(Grid& G, cudaStream_t st) {
 int adi_wave::create(const adi_wave_desc* desc, int n, const float* const* m,
                      const float* const* phi, const float* const* psi, const adi_source* src,
                      cudaStream_t st) {
-  if (n > 1) return fail(this, ADI_EUNSUPPORTED, "batched handles are created by adi_batch");
   if (!g_configured) {
     CK(configure_kernels(), "configure kernels");
     CK(configure_adjoint_kernels(), "configure adjoint kernels");
@@ -78,6 +77,74 @@ int adi_wave::create(const adi_wave_desc* desc, int n, const float* const* m,
     CK(cudaMemsetAsync(G.w, 0, bytes, st), "clear w");
     int rc = start_grid(s, m[s], phi[s], psi ? psi[s] : nullptr, src ? &src[s] : nullptr, st);
     if (rc != ADI_OK) return rc;
+  }
+  if (n > 1) return setup_batch(st);
+  return ADI_OK;
+}
+
+// Batched run: every shot advances `steps` steps; one persistent launch per
+// step (or the plain kernels per shot in batch mode 1), step pairs replayed
+// from a captured graph.
+int adi_wave::run_batch(int steps, const adi_source* src, cudaStream_t st) {
+  for (size_t s = 0; s < g.size(); ++s) {
+    Grid& G = g[s];
+    const adi_source none = {-1, -1, nullptr, 0};
+    const adi_source sr = src ? src[s] : none;
+    const bool on = sr.ix >= 0 && sr.wavelet != nullptr;
+    G.hgd.k = G.k;
+    G.hgd.k0 = G.k;
+    G.hgd.steps = steps;
+    G.hgd.wavelet = on ? sr.wavelet : nullptr;
+    G.hgd.n_wavelet = on ? sr.n_wavelet : 0;
+    G.hgd.src_ix = on ? sr.ix : -1;
+    G.hgd.src_iy = on ? sr.iy : -1;
+    G.hgd.n_rec = 0;
+    G.hgd.rec = nullptr;
+    G.hgd.traces = nullptr;
+    if (upload_gd(G, st) != ADI_OK) return ADI_ECUDA;
+  }
+  rr.valid = false;
+  const bool use_graph = g[0].plan.graph && !profile;
+  int t = 0;
+  if (use_graph) {
+    while (steps - t >= 2) {
+      cudaGraphExec_t& ex = pair[g[0].cur][0];
+      if (!ex) {
+        std::vector<int> cur0;
+        std::vector<long long> k0;
+        for (Grid& G : g) { cur0.push_back(G.cur); k0.push_back(G.k); }
+        const int64_t l0 = launches;
+        CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+        int rc = enqueue_batch_step(cap);
+        if (rc == ADI_OK) rc = enqueue_batch_step(cap);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cap, &graph);
+        for (size_t s = 0; s < g.size(); ++s) { g[s].cur = cur0[s]; g[s].k = k0[s]; }
+        const int64_t per_pair = launches - l0;
+        launches = l0;
+        if (rc != ADI_OK) {
+          if (graph) cudaGraphDestroy(graph);
+          return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(this, e, "end capture");
+        e = cudaGraphInstantiate(&ex, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+          ex = nullptr;
+          return cuda_fail(this, e, "graph instantiate");
+        }
+        pair_launches = per_pair;
+      }
+      CK(cudaGraphLaunch(ex, st), "graph launch");
+      launches += pair_launches;
+      for (Grid& G : g) { G.k += 2; G.from_init = false; }
+      t += 2;
+    }
+  }
+  while (t < steps) {
+    int rc = enqueue_batch_step(st);
+    if (rc != ADI_OK) return rc;
+    t += 1;
   }
   return ADI_OK;
 }
@@ -288,7 +355,7 @@ int adi_wave::run(int steps, const adi_source* src, const int32_t* rec_xy, int n
         (src[s].ix >= g[s].nx || src[s].iy < 0 || src[s].iy >= g[s].ny))
       return fail(this, ADI_EINVAL, "source node outside the grid");
   }
-  if (g.size() != 1) return fail(this, ADI_EUNSUPPORTED, "batched run");
+  if (g.size() != 1) return run_batch(steps, src, st);
   Grid& G = g[0];
   for (int r = 0; r < n_rec; ++r) {
     if (rec_xy[2 * r] < 0 || rec_xy[2 * r] >= G.nx || rec_xy[2 * r + 1] < 0 ||
@@ -469,6 +536,9 @@ adi_wave::~adi_wave() {
   if (d_err) cudaFree(d_err);
   if (scan) cudaFree(scan);
   if (d_rec) cudaFree(d_rec);
+  if (d_shots) cudaFree(d_shots);
+  if (d_items) cudaFree(d_items);
+  if (d_sync) cudaFree(d_sync);
   if (cap) cudaStreamDestroy(cap);
 }
 

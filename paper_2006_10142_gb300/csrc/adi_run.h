@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/adiwave.h"
+#include "adi_batch.h"
 #include "adi_internal.h"
 
 namespace adi {
@@ -24,6 +25,7 @@ struct GridPlan {
   bool fp64y = false;
   int graph = 1;
   bool tree = true;  // solver variant (see adi_sweeps.cuh)
+  int cta_threads = 0;
 };
 
 struct Grid {
@@ -86,7 +88,7 @@ struct adi_wave {
   int rec_cap = 0;
   cudaStream_t cap = nullptr;  // private stream used only for graph capture
   cudaGraphExec_t pair[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [orientation][gather]
-  adi_wave_tuning tuning = {0, 0, 0, 0, 0, 0, 0};
+  adi_wave_tuning tuning = {0, 0, 0, 0, 0, 0, 0, 0};
   int ckpt_every = 0;
   adi::RunRecord rr;
   adi::AdjWork aw;
@@ -95,6 +97,22 @@ struct adi_wave {
   std::vector<cudaEvent_t> ev_pool;
   int64_t launches = 0;
   std::string err;
+
+  // batched form (n_shots > 1)
+  bool batch_fp64 = false;
+  int batch_mode = 0;                 // 0: persistent kernel, 1: plain kernels per shot
+  adi::BatchShot* d_shots = nullptr;
+  int2* d_items = nullptr;
+  int n_items = 0;
+  int* d_sync = nullptr;              // [1 + n_shots]: ticket, x_done[]
+  int batch_grid = 0;
+  size_t batch_smem = 0;
+  long long spin_limit = 1ll << 22;
+  int never_ready = -1;
+  int64_t pair_launches = 0;
+  int setup_batch(cudaStream_t st);
+  int enqueue_batch_step(cudaStream_t st);
+  int run_batch(int steps, const adi_source* src, cudaStream_t st);
 
   int create(const adi_wave_desc* desc, int n, const float* const* m, const float* const* phi,
              const float* const* psi, const adi_source* src, cudaStream_t st);
