@@ -178,7 +178,8 @@ void adi_wave_destroy(adi_wave *h);
 /* Static text for a return code. */
 const char *adi_wave_strerror(int code);
 
-/* Detail of the last failing call on h (static empty string if none). */
+/* Detail of the last failing call on h (empty string if none); with h = NULL,
+ * the detail of the last failed adi_wave_init on the calling thread. */
 const char *adi_wave_last_error(const adi_wave *h);
 
 /* ---- tuning (the autotuner's knobs) -------------------------------------
@@ -197,9 +198,15 @@ const char *adi_wave_last_error(const adi_wave *h);
  *                   warp summaries) or ADI_SOLVER_CR_SMEM (cyclic reduction
  *                   level by level in shared memory, PCR for the last
  *                   `pcr_size` equations);
- * cta_threads:      upper bound on threads per CTA in both sweeps (64, 128,
- *                   256, 512 or 1024; smaller CTAs let two share an SM).
+ * cta_threads:      upper bound on threads per CTA of the x sweep (64, 128,
+ *                   256, 512 or 1024; smaller CTAs let several share an SM);
+ * cta_threads_y:    the same for the y sweep;
+ * y_stage:          how the y sweep fetches u^k, u^{k-1} for its update while
+ *                   it solves: ADI_STAGE_SMEM (asynchronous copies into
+ *                   shared memory) or ADI_STAGE_L2 (prefetch into L2, no
+ *                   shared memory, more CTAs per SM).
  * Zero fields mean "choose automatically". */
+enum { ADI_STAGE_AUTO = 0, ADI_STAGE_SMEM = 1, ADI_STAGE_L2 = 2 };
 enum { ADI_SOLVER_AUTO = 0, ADI_SOLVER_TREE = 1, ADI_SOLVER_CR_SMEM = 2 };
 typedef struct {
     int32_t chunk_x, chunk_y;
@@ -209,6 +216,8 @@ typedef struct {
     int32_t use_graph;
     int32_t solver;
     int32_t cta_threads;
+    int32_t cta_threads_y;
+    int32_t y_stage;
 } adi_wave_tuning;
 
 int adi_wave_get_tuning(const adi_wave *h, adi_wave_tuning *t);
@@ -220,7 +229,8 @@ int adi_wave_set_tuning(adi_wave *h, const adi_wave_tuning *t);
  * without graphs.  adi_wave_profile_read() waits for the handle's work,
  * sums the recorded durations per kind into ms[kind] and launch counts
  * into launches[kind] for kind < n_kinds, and clears the records.  Kinds:
- * 0 = x sweep (RHS + x solve), 1 = y sweep (+ update), 2 = other. */
+ * 0 = x sweep (RHS + x solve), 1 = y sweep (+ update), 2 = other (the
+ * batched persistent step). */
 enum { ADI_KERNEL_X = 0, ADI_KERNEL_Y = 1, ADI_KERNEL_OTHER = 2, ADI_KERNEL_KINDS = 3 };
 int adi_wave_profile(adi_wave *h, int32_t enable);
 int adi_wave_profile_read(adi_wave *h, double *ms, int64_t *launches,

@@ -60,7 +60,8 @@ class Tuning(ctypes.Structure):
     _fields_ = [("chunk_x", ctypes.c_int32), ("chunk_y", ctypes.c_int32),
                 ("rows_per_cta", ctypes.c_int32), ("cols_per_cta", ctypes.c_int32),
                 ("pcr_size", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("solver", ctypes.c_int32), ("cta_threads", ctypes.c_int32)]
+                ("solver", ctypes.c_int32), ("cta_threads", ctypes.c_int32),
+                ("cta_threads_y", ctypes.c_int32), ("y_stage", ctypes.c_int32)]
 
 
 class AdiError(RuntimeError):
@@ -132,10 +133,9 @@ def check(rc: int, handle=None, what: str = ""):
         return
     lib = load()
     msg = lib.adi_wave_strerror(rc).decode()
-    if handle:
-        detail = lib.adi_wave_last_error(handle).decode()
-        if detail:
-            msg += ": " + detail
+    detail = lib.adi_wave_last_error(handle if handle else None).decode()
+    if detail:
+        msg += ": " + detail
     if what:
         msg = what + ": " + msg
     raise AdiError(rc, msg)

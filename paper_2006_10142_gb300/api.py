@@ -292,6 +292,30 @@ class AdiWaveBatch:
     def profile(self, enable: bool = True):
         _lib.check(self._lib.adi_wave_profile(self._h, int(bool(enable))), self._h)
 
+    def profile_read(self):
+        ms = (ctypes.c_double * _lib.ADI_KERNEL_KINDS)()
+        cnt = (ctypes.c_int64 * _lib.ADI_KERNEL_KINDS)()
+        _lib.check(self._lib.adi_wave_profile_read(self._h, ms, cnt, _lib.ADI_KERNEL_KINDS), self._h)
+        return list(ms), list(cnt)
+
+    def reset(self, phis: Sequence[torch.Tensor], ms=None, stream=None):
+        """Re-run the start-up (Eq. CN2) of every shot in place."""
+        n = self.n
+        pp = (ctypes.c_void_p * n)()
+        mp = (ctypes.c_void_p * n)() if ms is not None else None
+        keep = []
+        for b in range(n):
+            phi = _dev_f32(phis[b], "phi[%d]" % b, self.shapes[b])
+            keep.append(phi)
+            pp[b] = phi.data_ptr()
+            if ms is not None:
+                m = _dev_f32(ms[b], "m[%d]" % b, self.shapes[b])
+                keep.append(m)
+                mp[b] = m.data_ptr()
+        self._keep = keep
+        rc = self._lib.adi_wave_reset(self._h, mp, pp, None, None, _stream_ptr(stream))
+        _lib.check(rc, self._h, "reset (batch)")
+
     def launch_count(self) -> int:
         return int(self._lib.adi_wave_launch_count(self._h))
 

@@ -67,6 +67,8 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
   P.pcr = pcr;
 
   const int ct = t.cta_threads;
+  const int cty = t.cta_threads_y;
+  if (cty != 0 && cty != 64 && cty != 128 && cty != 256 && cty != 512 && cty != 1024) { why = "cta_threads_y must be 64..1024, a power of two"; return ADI_EINVAL; }
   if (ct != 0 && ct != 64 && ct != 128 && ct != 256 && ct != 512 && ct != 1024) { why = "cta_threads must be 64..1024, a power of two"; return ADI_EINVAL; }
   // ---- x sweep
   {
@@ -93,7 +95,7 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
   }
   // ---- y sweep
   {
-    const int maxT = std::min(P.fp64y ? 512 : 1024, ct ? ct : 1024);
+    const int maxT = std::min(P.fp64y ? 512 : 1024, cty ? cty : 1024);
     const int maxC = 16;
     int W = t.cols_per_cta ? t.cols_per_cta : 8;
     if (W != 4 && W != 8 && W != 16 && W != 32) { why = "cols_per_cta must be 4, 8, 16 or 32"; return ADI_EINVAL; }
@@ -125,8 +127,21 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
     int tcol, C;
     geom(K, tcol, C);
     if (!fits(K)) { why = "ny too large for this chunk_y (cluster or top system)"; return ADI_EUNSUPPORTED; }
-    if (align64(y_smem_bytes(W, C, tcol, P.fp64y, P.tree)) + y_stage_bytes(W * tcol, K) >
-        (size_t)kMaxDynSmem) { why = "y sweep shared memory too large"; return ADI_EUNSUPPORTED; }
+    const size_t ysm = align64(y_smem_bytes(W, C, tcol, P.fp64y, P.tree));
+    const size_t ystage = y_stage_bytes(W * tcol, K);
+    if (t.y_stage < ADI_STAGE_AUTO || t.y_stage > ADI_STAGE_L2) { why = "unknown y_stage"; return ADI_EINVAL; }
+    int stage = t.y_stage;
+    if (stage == ADI_STAGE_AUTO) {
+      // shared-memory staging unless it would keep a second CTA off the SM
+      const int by_regs = std::max(1, 65536 / (64 * W * tcol));
+      const size_t per_sm = 228 * 1024;
+      stage = (std::min(by_regs, 2) * (ysm + ystage + 1024) <= per_sm) ? ADI_STAGE_SMEM : ADI_STAGE_L2;
+    }
+    if (ysm + (stage == ADI_STAGE_SMEM ? ystage : 0) > (size_t)kMaxDynSmem) {
+      why = "y sweep shared memory too large";
+      return ADI_EUNSUPPORTED;
+    }
+    P.y_stage = stage;
     P.ky = K;
     P.log2W = ilog2(W);
     P.log2tcol = ilog2(tcol);
@@ -134,6 +149,7 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
   }
   P.graph = (t.use_graph >= 0) ? 1 : 0;
   P.cta_threads = ct;
+  P.cta_threads_y = cty;
   G.plan = P;
   return ADI_OK;
 }
@@ -160,8 +176,11 @@ extern "C" const char* adi_wave_strerror(int code) {
   }
 }
 
+// Detail of the last adi_wave_init failure on this thread (the handle is gone).
+static thread_local std::string g_init_error;
+
 extern "C" const char* adi_wave_last_error(const adi_wave* h) {
-  return h ? h->err.c_str() : "";
+  return h ? h->err.c_str() : g_init_error.c_str();
 }
 
 extern "C" int adi_wave_init(adi_wave** out, const adi_wave_desc* desc, int32_t n_shots,
@@ -184,6 +203,7 @@ extern "C" int adi_wave_init(adi_wave** out, const adi_wave_desc* desc, int32_t 
   if (!h) return ADI_ENOMEM;
   int rc = h->create(desc, n_shots, m, phi, psi, src, (cudaStream_t)stream);
   if (rc != ADI_OK) {
+    g_init_error = h->err;
     delete h;
     return rc;
   }
@@ -264,6 +284,8 @@ extern "C" int adi_wave_get_tuning(const adi_wave* h, adi_wave_tuning* t) {
   t->use_graph = P.graph ? 1 : -1;
   t->solver = P.tree ? ADI_SOLVER_TREE : ADI_SOLVER_CR_SMEM;
   t->cta_threads = P.cta_threads;
+  t->cta_threads_y = P.cta_threads_y;
+  t->y_stage = P.y_stage;
   return ADI_OK;
 }
 

@@ -89,13 +89,20 @@ cudaError_t launch_batch(const BatchArgs& a, bool fp64, int grid, size_t smem, c
               : launch_batch_t<kBatchK, float, 1024>(a, grid, smem, st);
 }
 
+// The per-block limit covers static plus dynamic shared memory.
+template <typename KernT>
+static cudaError_t allow_dyn_smem(KernT kern) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              kMaxDynSmem - (int)fa.sharedSizeBytes);
+}
+
 cudaError_t configure_batch_kernels(int* blocks_per_sm_f32, int* blocks_per_sm_f64, size_t smem_f32,
                                     size_t smem_f64) {
-  cudaError_t e = cudaFuncSetAttribute(batch_step_kernel<kBatchK, float, 1024, true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(batch_step_kernel<kBatchK, double, 512, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+  cudaError_t e = allow_dyn_smem(batch_step_kernel<kBatchK, float, 1024, true>);
+  if (e == cudaSuccess) e = allow_dyn_smem(batch_step_kernel<kBatchK, double, 512, true>);
   if (e == cudaSuccess && blocks_per_sm_f32)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         blocks_per_sm_f32, batch_step_kernel<kBatchK, float, 1024, true>, 1024, smem_f32);

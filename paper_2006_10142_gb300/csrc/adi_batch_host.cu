@@ -75,11 +75,13 @@ int adi_wave::setup_batch(cudaStream_t st) {
       ya.sc = G.dt * G.dt / (2.0 * G.hy * G.hy);
       ya.gd = G.gd; ya.err = d_err;
       ya.stage_off = (int)ysm;
+      ya.stage_mode = 1;
     }
     for (int i = 0; i < B.x_items; ++i) xitems.push_back(make_int2(s, i << 1));
     for (int i = 0; i < B.y_items; ++i) yitems.push_back(make_int2(s, (i << 1) | 1));
   }
-  if (smem > (size_t)kMaxDynSmem) return fail(this, ADI_EUNSUPPORTED, "batched kernel shared memory");
+  if (smem + 512 > (size_t)kMaxDynSmem)  // 512: the kernel's static shared variables
+    return fail(this, ADI_EUNSUPPORTED, "batched kernel shared memory");
   std::vector<int2> items = xitems;
   items.insert(items.end(), yitems.begin(), yitems.end());
   n_items = (int)items.size();
@@ -121,7 +123,10 @@ int adi_wave::enqueue_batch_step(cudaStream_t st) {
     a.err = d_err;
     a.spin_limit = spin_limit;
     a.never_ready_shot = never_ready;
+    cudaEvent_t ev = nullptr;
+    if (profile && prof_begin(st, &ev) != ADI_OK) return ADI_ECUDA;
     CKB(launch_batch(a, batch_fp64, batch_grid, batch_smem, st), "batched step launch");
+    if (profile && prof_end(st, ev, ADI_KERNEL_OTHER) != ADI_OK) return ADI_ECUDA;
     launches += 1;
   }
   for (Grid& G : g) {

@@ -107,12 +107,24 @@ __device__ __forceinline__ void y_strip_body(const YArgs& a, int strip, int rank
   const size_t base = (size_t)j0 * ld + i;
   const T sc = (T)a.sc;
 
-  // Stage u^k and u^{k-1} of this thread's rows into shared memory with
-  // asynchronous copies issued now, so that their HBM traffic overlaps the
-  // solve; the epilogue reads them back.  Layout [2][K][threads].
+  // Fetch u^k and u^{k-1} of this thread's rows now, so that their HBM
+  // traffic overlaps the solve: either asynchronous copies into shared memory
+  // (layout [2][K][threads], read back by the epilogue) or, with
+  // stage_off < 0, prefetches into L2 (one per row segment of the strip).
   const int threads = blockDim.x;
-  float* stage = reinterpret_cast<float*>(smem + a.stage_off);
-  {
+  const bool smem_stage = a.stage_off >= 0;
+  float* stage = reinterpret_cast<float*>(smem + (smem_stage ? a.stage_off : 0));
+  if (!smem_stage) {
+    if (col == 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if (j0 + k < a.ny) {
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(a.u_cur + base + k * ld));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(a.u_prev + base + k * ld));
+        }
+      }
+    }
+  } else {
     const uint32_t sb = (uint32_t)__cvta_generic_to_shared(stage + tid);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -145,13 +157,15 @@ __device__ __forceinline__ void y_strip_body(const YArgs& a, int strip, int rank
   }
   y_solve_cols<K, T, TREE>(smem, a.log2W, a.log2tcol, C, rank, a.pcr, col, gq, d, s);
 
-  asm volatile("cp.async.wait_all;" ::: "memory");  // this thread's staged rows
+  if (smem_stage) asm volatile("cp.async.wait_all;" ::: "memory");  // this thread's staged rows
   bool bad = false;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     if (full || (colok && (j0 + k) < a.ny)) {
       const size_t idx = base + k * ld;
-      const float un = 2.0f * stage[k * threads + tid] - stage[(K + k) * threads + tid] + (float)d[k];
+      const float uc = smem_stage ? stage[k * threads + tid] : __ldcg(a.u_cur + idx);
+      const float up = smem_stage ? stage[(K + k) * threads + tid] : __ldcg(a.u_prev + idx);
+      const float un = 2.0f * uc - up + (float)d[k];
       a.u_prev[idx] = un;
       if (a.z_out) a.z_out[idx] = (float)d[k];
       bad |= !isfinite(un);

@@ -153,11 +153,12 @@ static cudaError_t launch_y_t(const YArgs& a_in, cudaStream_t st) {
   const int threads = W << a.log2tcol;
   if (threads % 32 != 0 || threads > MAXT) return cudaErrorInvalidValue;  // whole warps only
   const int strips = (a.nx + W - 1) / W;
-  a.stage_off = (int)align64(y_smem_bytes(W, a.C, 1 << a.log2tcol, sizeof(T) == 8, TREE));
+  const size_t ysm = align64(y_smem_bytes(W, a.C, 1 << a.log2tcol, sizeof(T) == 8, TREE));
+  a.stage_off = (a.stage_mode == 2) ? -1 : (int)ysm;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(strips * a.C, 1, 1);
   cfg.blockDim = dim3(threads, 1, 1);
-  cfg.dynamicSmemBytes = a.stage_off + y_stage_bytes(threads, K);
+  cfg.dynamicSmemBytes = ysm + (a.stage_off >= 0 ? y_stage_bytes(threads, K) : 0);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;

@@ -53,7 +53,8 @@ struct YArgs {
   double sc;           // tau^2 / (2 h2^2)
   GridDev* gd;         // k is advanced by one CTA
   int* err;
-  int stage_off;       // byte offset of the u^k / u^{k-1} staging area in shared memory
+  int stage_off;       // byte offset of the u^k / u^{k-1} staging area in shared memory, -1: L2
+  int stage_mode;      // 1: shared-memory staging, 2: L2 prefetch (launchers set stage_off)
 };
 
 // Launchers (adi_forward.cu).

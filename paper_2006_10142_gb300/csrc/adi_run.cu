@@ -289,6 +289,8 @@ int adi_wave::launch_fwd(Grid& G, const float* u_cur, float* u_prev, float* w, f
   ya.u_cur = u_cur;
   ya.u_prev = u_prev;
   ya.z_out = z_out;
+  ya.stage_mode = P.y_stage;
+  ya.stage_off = 0;
   ya.sc = G.dt * G.dt / (2.0 * G.hy * G.hy);
   ya.gd = gd;
   ya.err = d_err;
