@@ -44,14 +44,17 @@ WORKLOADS = {
     "ricker_16384": dict(n=16384, time_steps=200, kind="ricker"),
     "ricker_4096": dict(n=4096, time_steps=1000, kind="ricker"),
     "standing_wave_128": dict(n=128, time_steps=200, kind="standing"),
+    "batch_64_shots": dict(count=64, time_steps=500, kind="batch"),
+    "adjoint_1024": dict(n=1024, time_steps=2000, n_rec=64, ckpt_every=50, kind="adjoint"),
 }
 METRIC = "ADI grid-point updates/sec"
 UNIT = "grid-point updates/s"
 # algorithmic HBM bytes per grid point per launch (FP32 fields)
 BYTES_X = 12  # read u^k, m; write w
 BYTES_Y = 20  # read w, m, u^k, u^{k-1}; write u^{k+1}
-# dram__bytes_read.sum + dram__bytes_write.sum per launch from the ncu capture
-# summarised in profiles/ (None until measured for the current kernels)
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
+# kernel from the ncu capture summarised in profiles/ (absent until measured
+# for the current kernels)
 NCU_TRAFFIC = {}
 
 
@@ -213,6 +216,7 @@ def main():
     ap.add_argument("--workload", default="ricker_16384", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -231,8 +235,84 @@ def main():
     dev = torch.device("cuda", local_rank)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
-    from paper_2006_10142_gb300 import api
+    ctx = dict(args=args, wl=wl, world=world, rank=rank, local_rank=local_rank, dev=dev,
+               dist=dist)
+    if wl["kind"] == "batch":
+        out = run_batch(ctx)
+    elif wl["kind"] == "adjoint":
+        out = run_adjoint(ctx)
+    else:
+        out = run_single(ctx)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
+
+def _clock_sampler(ctx):
+    vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    lr = ctx["local_rank"]
+    return ClockSampler(vis[lr].strip() if lr < len(vis) else lr)
+
+
+def _timed(ctx, step_fn, launch_count):
+    """Warm-up, then K steps between barriers + syncs, timed by CUDA events on
+    the launching stream; returns (max_ms over ranks, own ms, launches, clocks)."""
+    import torch
+    args, world, rank, dist = ctx["args"], ctx["world"], ctx["rank"], ctx["dist"]
+    stream = torch.cuda.current_stream()
+    clocks = _clock_sampler(ctx)
+    if rank == 0:
+        clocks.start()
+        time.sleep(0.5)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step_fn()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = launch_count() - l0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop() if rank == 0 else None
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], dtype=torch.float64, device=ctx["dev"])
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item()), ms, launches, clk
+
+
+def _max_over_ranks(ctx, v):
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=ctx["dev"])
+    if ctx["world"] > 1:
+        ctx["dist"].all_reduce(t, op=ctx["dist"].ReduceOp.MAX)
+    return float(t.item())
+
+
+def _roofline(kms, kcnt, kinds, alg_bytes):
+    """Dominant kernel's algorithmic GB/s against the measured copy bandwidth."""
+    peak, peak_kind = measured_peak_gbs()
+    k = max(kinds, key=lambda q: kms[q])
+    per_launch_ms = kms[k] / max(kcnt[k], 1)
+    achieved = alg_bytes[k] / (per_launch_ms / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": kinds[k], "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+            "traffic": NCU_TRAFFIC.get(kinds[k]), "alg_bytes_per_launch": alg_bytes[k],
+            "avg_launch_ms": per_launch_ms,
+            "kernel_ms": {kinds[q]: kms[q] for q in kinds},
+            "kernel_launches": {kinds[q]: kcnt[q] for q in kinds}}
+
+
+def run_single(ctx):
+    import torch
+    from paper_2006_10142_gb300 import api, autotune
+    args, wl, world, rank, dev = ctx["args"], ctx["wl"], ctx["world"], ctx["rank"], ctx["dev"]
     n, ts = wl["n"], wl["time_steps"]
     prob = make_problem(wl)
     m_d = torch.from_numpy(prob.m).to(dev)
@@ -240,6 +320,9 @@ def main():
     src = prob.src
     wav_d = torch.from_numpy(prob.wavelet.astype(np.float32)).to(dev) if prob.wavelet is not None else None
     h = api.AdiWave(m_d, phi_d, prob.tau, src=src, wavelet=wav_d)
+    tuned = None
+    if not args.no_autotune:
+        tuned = autotune.apply(h, steps=2, warmup=1)
 
     def bench_step():
         h.reset(phi_d)
@@ -248,49 +331,17 @@ def main():
     for _ in range(max(args.warmup, 0)):
         bench_step()
     h.sync_status()
-    stream = torch.cuda.current_stream()
     h.profile(True)
     h.profile_read()
-    vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
-    clocks = ClockSampler(vis[local_rank].strip() if local_rank < len(vis) else local_rank)
-    if rank == 0:
-        clocks.start()
-        time.sleep(0.5)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    l0 = h.launch_count()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        bench_step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    launches = h.launch_count() - l0
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop() if rank == 0 else None
-    elapsed_ms = ev0.elapsed_time(ev1)
+    max_ms, _, launches, clk = _timed(ctx, bench_step, h.launch_count)
     kms, kcnt = h.profile_read()
     h.profile(False)
     h.sync_status()
-    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms = float(t.item())
     value = world * n * n * ts * args.steps / (max_ms / 1e3)
+    roof = _roofline(kms, kcnt, {0: "x_sweep_kernel", 1: "y_sweep_kernel"},
+                     {0: BYTES_X * n * n, 1: BYTES_Y * n * n})
+    roof["step_gbs_32B"] = 32.0 * n * n * ts * args.steps / (max_ms / 1e3) / 1e9
 
-    # roofline of the dominant kernel
-    peak, peak_kind = measured_peak_gbs()
-    kind = 0 if kms[0] >= kms[1] else 1
-    name = "x_sweep_kernel" if kind == 0 else "y_sweep_kernel"
-    per_launch_ms = kms[kind] / max(kcnt[kind], 1)
-    alg_bytes = (BYTES_X if kind == 0 else BYTES_Y) * n * n
-    achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
-    traffic = NCU_TRAFFIC.get((name, args.workload))
-
-    # end to end through the public API from pinned host buffers
     e2e = None
     if not args.no_e2e:
         m_h = torch.from_numpy(prob.m).pin_memory()
@@ -315,53 +366,148 @@ def main():
         e2e_step()
         torch.cuda.synchronize()
         if world > 1:
-            dist.barrier()
+            ctx["dist"].barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             e2e_step()
         torch.cuda.synchronize()
-        e_dt = time.perf_counter() - t0
-        te = torch.tensor([e_dt], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e_dt = _max_over_ranks(ctx, time.perf_counter() - t0)
         bi = m_h.numel() * 4 + phi_h.numel() * 4 + (wav_h.numel() * 4 if wav_h is not None else 0)
-        e2e = {"value": world * n * n * ts * args.steps / float(te.item()), "unit": UNIT,
+        e2e = {"value": world * n * n * ts * args.steps / e_dt, "unit": UNIT,
                "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(n * n * 4)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(prob, wl)
-
+    out = None
     if rank == 0:
-        tun = h.tuning()
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "time_steps": ts,
-                       "medium": "seeded c-field 1 + 2 sigmoid(8 Gaussian bumps), m = c^2",
+                       "medium": "seeded c-field 1 + 2 sigmoid(8 Gaussian bumps), m = c^2"
+                       if wl["kind"] == "ricker" else "c = 1",
                        "source": "Ricker f=20" if wl["kind"] == "ricker" else "none",
                        "l2": "inputs larger than L2 (4 FP32 fields of %.0f MiB)" % (n * n * 4 / 2**20),
                        "timed_launches": "direct launches with per-kernel CUDA events",
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "tuning": tun},
-            "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                         "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
-                         "avg_launch_ms": per_launch_ms,
-                         "kernel_ms": {"x_sweep_kernel": kms[0], "y_sweep_kernel": kms[1]},
-                         "kernel_launches": {"x_sweep_kernel": kcnt[0], "y_sweep_kernel": kcnt[1]},
-                         "step_gbs_32B": 32.0 * n * n * ts * args.steps / (max_ms / 1e3) / 1e9},
-            "gpu_launches": int(launches),
-            "clocks": clk,
-            "e2e": e2e,
+                       "tuning": h.tuning(), "autotuned": tuned is not None},
+            "roofline": roof, "gpu_launches": int(launches), "clocks": clk, "e2e": e2e,
             "cpu_baseline": cpu,
         }
-        print(json.dumps(out), flush=True)
     h.close()
-    if world > 1:
-        dist.destroy_process_group()
+    return out
+
+
+def run_batch(ctx):
+    """64 shots with n from {256, 512, 1024, 2048}, one persistent launch per step;
+    the plain kernels launched per shot are timed beside it for comparison."""
+    import torch
+    from paper_2006_10142_gb300 import api, inputs, shard
+    args, wl, world, rank, dev = ctx["args"], ctx["wl"], ctx["world"], ctx["rank"], ctx["dev"]
+    ts = wl["time_steps"]
+    sizes_all = inputs.batch_sizes(wl["count"], seed=0)
+    mine = shard.local_shots([(s, s) for s in sizes_all], rank, world)
+    probs = [inputs.ricker_problem(sizes_all[b], ts, seed=b, m_dtype=np.float32) for b in mine]
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+    ms_ = [t(p.m) for p in probs]
+    phis = [t(p.phi) for p in probs]
+    wavs = [t(p.wavelet) for p in probs]
+    srcs = [p.src for p in probs]
+    B = api.AdiWaveBatch(ms_, phis, [p.tau for p in probs])
+    pts = sum(p.n * p.n for p in probs)
+    pts_all = sum(s * s for s in sizes_all)
+
+    def bench_step():
+        B.reset(phis)
+        B.run(ts, srcs=srcs, wavelets=wavs)
+
+    for _ in range(max(args.warmup, 0)):
+        bench_step()
+    B.sync_status()
+    B.profile(True)
+    B.profile_read()
+    max_ms, _, launches, clk = _timed(ctx, bench_step, B.launch_count)
+    kms, kcnt = B.profile_read()
+    B.profile(False)
+    B.sync_status()
+    roof = _roofline(kms, kcnt, {2: "batch_step_kernel"}, {2: 32 * pts})
+    # the plain single-grid kernels, one launch per shot and sweep, same work
+    B.set_mode(1)
+    for _ in range(2):
+        bench_step()
+    plain_ms, _, _, _ = _timed(ctx, bench_step, B.launch_count)
+    B.set_mode(0)
+    value = pts_all * ts * args.steps / (max_ms / 1e3)
+    out = None
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic",
+               "config": {"workload": args.workload, "shots": len(sizes_all),
+                          "points_per_step": pts_all, "time_steps": ts,
+                          "l2": "inputs larger than L2 (%.0f MiB per field over all shots)"
+                          % (pts_all * 4 / 2**20),
+                          "parallelism": "shot-sharded" if world > 1 else "single GPU",
+                          "plain_per_shot_value": pts_all * ts * args.steps / (plain_ms / 1e3)},
+               "roofline": roof, "gpu_launches": int(launches), "clocks": clk, "e2e": None,
+               "cpu_baseline": None}
+    B.close()
+    return out
+
+
+def run_adjoint(ctx):
+    """1024^2, 64 receivers, 2000 steps, checkpoint every 50: time of the
+    gradient (adjoint sweep with recomputation) per time step."""
+    import torch
+    from paper_2006_10142_gb300 import api, inputs
+    args, wl, world, rank, dev = ctx["args"], ctx["wl"], ctx["world"], ctx["rank"], ctx["dev"]
+    n, ts, every = wl["n"], wl["time_steps"], wl["ckpt_every"]
+    prob, m_true = inputs.adjoint_problem(n, ts, seed=0, n_rec=wl["n_rec"])
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+    wav = t(prob.wavelet)
+    zeros = torch.zeros((n, n), dtype=torch.float32, device=dev)
+    obs = api.AdiWave(t(m_true), zeros, prob.tau, src=prob.src, wavelet=wav)
+    d = obs.run(ts, src=prob.src, wavelet=wav, rec=prob.rec)
+    obs.close()
+    h = api.AdiWave(t(prob.m), zeros, prob.tau, src=prob.src, wavelet=wav)
+    h.set_checkpointing(every)
+    state = {}
+
+    def forward():
+        h.reset(zeros)
+        state["tr"] = h.run(ts, src=prob.src, wavelet=wav, rec=prob.rec)
+
+    def grad():
+        state["g"] = h.adjoint(state["tr"] - d, ckpt_every=every)
+
+    for _ in range(max(args.warmup, 1)):
+        forward()
+        grad()
+    torch.cuda.synchronize()
+    f_ms, _, _, _ = _timed(ctx, forward, h.launch_count)
+    forward()
+    adj_ms, _, launches, clk = _timed(ctx, grad, h.launch_count)
+    h.sync_status()
+    out = None
+    if rank == 0:
+        per_step = adj_ms / args.steps / ts
+        out = {"metric": "adjoint gradient time/step", "value": per_step, "unit": "ms",
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": adj_ms / args.steps, "higher_is_better": False,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 gradient)",
+               "data": "synthetic",
+               "config": {"workload": args.workload, "n": n, "time_steps": ts,
+                          "receivers": wl["n_rec"], "ckpt_every": every,
+                          "forward_ms_per_time_step": f_ms / args.steps / ts,
+                          "adjoint_over_forward": (adj_ms / f_ms) if f_ms > 0 else None},
+               "roofline": None, "gpu_launches": int(launches), "clocks": clk, "e2e": None,
+               "cpu_baseline": None}
+    h.close()
+    return out
 
 
 if __name__ == "__main__":
