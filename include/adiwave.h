@@ -204,7 +204,10 @@ const char *adi_wave_last_error(const adi_wave *h);
  * y_stage:          how the y sweep fetches u^k, u^{k-1} for its update while
  *                   it solves: ADI_STAGE_SMEM (asynchronous copies into
  *                   shared memory) or ADI_STAGE_L2 (prefetch into L2, no
- *                   shared memory, more CTAs per SM).
+ *                   shared memory, more CTAs per SM);
+ * persist:          1 = one wave of resident CTAs (clusters) loops over the
+ *                   tiles of each sweep and prefetches its next tile into L2
+ *                   while solving the current one; -1 = one CTA per tile.
  * Zero fields mean "choose automatically". */
 enum { ADI_STAGE_AUTO = 0, ADI_STAGE_SMEM = 1, ADI_STAGE_L2 = 2 };
 enum { ADI_SOLVER_AUTO = 0, ADI_SOLVER_TREE = 1, ADI_SOLVER_CR_SMEM = 2 };
@@ -218,6 +221,7 @@ typedef struct {
     int32_t cta_threads;
     int32_t cta_threads_y;
     int32_t y_stage;
+    int32_t persist;
 } adi_wave_tuning;
 
 int adi_wave_get_tuning(const adi_wave *h, adi_wave_tuning *t);

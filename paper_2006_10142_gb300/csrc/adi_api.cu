@@ -150,6 +150,8 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
   P.graph = (t.use_graph >= 0) ? 1 : 0;
   P.cta_threads = ct;
   P.cta_threads_y = cty;
+  if (t.persist < -1 || t.persist > 1) { why = "persist must be -1, 0 or 1"; return ADI_EINVAL; }
+  P.persist = t.persist > 0 ? 1 : 0;
   G.plan = P;
   return ADI_OK;
 }
@@ -286,6 +288,7 @@ extern "C" int adi_wave_get_tuning(const adi_wave* h, adi_wave_tuning* t) {
   t->cta_threads = P.cta_threads;
   t->cta_threads_y = P.cta_threads_y;
   t->y_stage = P.y_stage;
+  t->persist = P.persist ? 1 : -1;
   return ADI_OK;
 }
 

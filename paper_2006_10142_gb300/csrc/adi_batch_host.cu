@@ -68,6 +68,7 @@ int adi_wave::setup_batch(cudaStream_t st) {
       xa.sc = G.dt * G.dt / (2.0 * G.hx * G.hx);
       xa.src_scale = G.dt * G.dt / (G.hx * G.hy);
       xa.gd = G.gd;
+      xa.persist = 0;
       YArgs& ya = B.ya[c];
       ya.nx = G.nx; ya.ny = G.ny; ya.ld = G.ld;
       ya.log2W = ilog2(W); ya.log2tcol = ilog2(tcol); ya.C = 1; ya.pcr = 32;
@@ -76,6 +77,7 @@ int adi_wave::setup_batch(cudaStream_t st) {
       ya.gd = G.gd; ya.err = d_err;
       ya.stage_off = (int)ysm;
       ya.stage_mode = 1;
+      ya.persist = 0;
     }
     for (int i = 0; i < B.x_items; ++i) xitems.push_back(make_int2(s, i << 1));
     for (int i = 0; i < B.y_items; ++i) yitems.push_back(make_int2(s, (i << 1) | 1));

@@ -85,6 +85,37 @@ __device__ __forceinline__ void x_rows_body(const XArgs& a, int blk, unsigned ch
   if (active) store_vec<K, T>(a.w + row + i0, d);
 }
 
+// L2 prefetch of the rows of block `blk` (u^k and m; the halo rows of a block
+// are the neighbouring blocks' own rows).  One instruction per thread chunk.
+template <int K>
+__device__ __forceinline__ void x_prefetch_rows(const XArgs& a, int blk) {
+  const int tsys = 1 << a.log2tsys;
+  const int sys = threadIdx.x >> a.log2tsys;
+  const int i0 = (threadIdx.x & (tsys - 1)) * K;
+  const int j = blk * a.spc + sys;
+  if (j < a.ny && i0 < a.nx) {
+    const size_t off = (size_t)j * a.ld + i0;
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.u + off));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.m + off));
+  }
+}
+
+// L2 prefetch of this CTA's rows of strip `strip` (w, m, u^k, u^{k-1}): the
+// threads of columns 0..3 take one field each, one instruction per row.
+template <int K>
+__device__ __forceinline__ void y_prefetch_strip(const YArgs& a, int strip, int rank) {
+  const int W = 1 << a.log2W;
+  const int col = threadIdx.x & (W - 1);
+  if (col >= 4) return;
+  const int q = threadIdx.x >> a.log2W;
+  const int j0 = (rank * (1 << a.log2tcol) + q) * K;
+  const float* f = col == 0 ? a.w : col == 1 ? a.m : col == 2 ? a.u_cur : a.u_prev;
+  const size_t base = (size_t)j0 * a.ld + (size_t)strip * W;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (j0 + k < a.ny) asm volatile("prefetch.global.L2 [%0];" ::"l"(f + base + (size_t)k * a.ld));
+}
+
 // Strip `strip` of 2^log2W columns, cluster rank `rank` of C along the
 // column (C = 1 outside clusters).  `bump` advances the grid's level k (one
 // CTA per grid and step does it).  A kernel with C > 1 must have executed

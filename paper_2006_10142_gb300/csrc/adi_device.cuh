@@ -310,9 +310,15 @@ __device__ __forceinline__ Seg<T> warp_tree_up(Seg<T> S, Node<T>* nodes, int lan
     Seg<T> P;
     P.f = shfl_xor_eq(S.f, m);
     P.l = shfl_xor_eq(S.l, m);
+    // order the pair with selects (not a branch: the lanes of a warp differ)
+    const bool right = (lane & m) != 0;
+    Seg<T> L, R;
+    L.f = right ? P.f : S.f;
+    L.l = right ? P.l : S.l;
+    R.f = right ? S.f : P.f;
+    R.l = right ? S.l : P.l;
     Node<T> nd;
-    if (lane & m) S = seg_merge(P, S, nd);
-    else S = seg_merge(S, P, nd);
+    S = seg_merge(L, R, nd);
     if ((lane & (2 * m - 1)) == 0) nodes[node_slot(t, lane)] = nd;
   }
   __syncwarp();

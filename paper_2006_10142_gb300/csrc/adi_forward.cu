@@ -27,7 +27,18 @@ namespace adi {
 template <int K, typename T, int MAXT, bool TREE>
 __global__ void __launch_bounds__(MAXT, 1) x_sweep_kernel(const XArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  x_rows_body<K, T, TREE>(a, blockIdx.x, smem);
+  if (!a.persist) {
+    x_rows_body<K, T, TREE>(a, blockIdx.x, smem);
+    return;
+  }
+  // persistent: loop over row blocks; prefetch the next block's rows of u^k
+  // and m into L2 while this one is solved
+  const int nblk = (a.ny + a.spc - 1) / a.spc;
+  for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    if (blk + (int)gridDim.x < nblk) x_prefetch_rows<K>(a, blk + gridDim.x);
+    x_rows_body<K, T, TREE>(a, blk, smem);
+    __syncthreads();  // shared memory is reused by the next block
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -37,8 +48,25 @@ __global__ void __launch_bounds__(MAXT, 1) x_sweep_kernel(const XArgs a) {
 template <int K, typename T, int MAXT, bool TREE>
 __global__ void __launch_bounds__(MAXT, 1) y_sweep_kernel(const YArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  cluster_arrive_early(a.C);
-  y_strip_body<K, T, TREE>(a, blockIdx.x / a.C, cluster_rank(a.C), blockIdx.x == 0, smem);
+  const int rank = cluster_rank(a.C);
+  if (!a.persist) {
+    cluster_arrive_early(a.C);
+    y_strip_body<K, T, TREE>(a, blockIdx.x / a.C, rank, blockIdx.x == 0, smem);
+    return;
+  }
+  // persistent: each cluster loops over strips; the next strip's rows of this
+  // CTA are prefetched into L2 while the current one is solved.  Every
+  // iteration arrives once on the cluster barrier to pair with the wait in
+  // y_solve_cols.
+  const int W = 1 << a.log2W;
+  const int nstrips = (a.nx + W - 1) / W;
+  const int nclusters = gridDim.x / a.C;
+  for (int strip = blockIdx.x / a.C; strip < nstrips; strip += nclusters) {
+    cluster_arrive_early(a.C);
+    if (strip + nclusters < nstrips) y_prefetch_strip<K>(a, strip + nclusters, rank);
+    y_strip_body<K, T, TREE>(a, strip, rank, strip == 0 && rank == 0, smem);
+    __syncthreads();  // shared memory is reused by the next strip
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -140,8 +168,17 @@ template <int K, typename T, int MAXT, bool TREE>
 static cudaError_t launch_x_t(const XArgs& a, cudaStream_t st) {
   const int threads = a.spc << a.log2tsys;
   if (threads % 32 != 0 || threads > MAXT) return cudaErrorInvalidValue;  // whole warps only
-  const int blocks = (a.ny + a.spc - 1) / a.spc;
+  int blocks = (a.ny + a.spc - 1) / a.spc;
   const size_t sm = x_smem_bytes(a.spc, 1 << a.log2tsys, sizeof(T) == 8, TREE);
+  if (a.persist) {  // one wave of resident CTAs
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, x_sweep_kernel<K, T, MAXT, TREE>, threads, sm);
+    if (e != cudaSuccess) return e;
+    blocks = std::max(1, std::min(blocks, nsm * std::max(per_sm, 1)));
+  }
   x_sweep_kernel<K, T, MAXT, TREE><<<blocks, threads, sm, st>>>(a);
   return cudaGetLastError();
 }
@@ -167,6 +204,12 @@ static cudaError_t launch_y_t(const YArgs& a_in, cudaStream_t st) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if (a.persist) {  // one wave of resident clusters
+    int nc = 0;
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&nc, y_sweep_kernel<K, T, MAXT, TREE>, &cfg);
+    if (e != cudaSuccess) return e;
+    cfg.gridDim = dim3(std::max(1, std::min(strips, nc)) * a.C, 1, 1);
+  }
   return cudaLaunchKernelEx(&cfg, y_sweep_kernel<K, T, MAXT, TREE>, a);
 }
 

@@ -36,6 +36,7 @@ struct XArgs {
   double sc;        // tau^2 / (2 h1^2): s = sc * m
   double src_scale; // tau^2 / (h1 h2)
   const GridDev* gd;
+  int persist;      // 1: persistent CTAs loop over row blocks (grid set by the launcher)
 };
 
 // Arguments of the y-sweep + update kernel (Eq. fr2's y operator).
@@ -55,6 +56,7 @@ struct YArgs {
   int* err;
   int stage_off;       // byte offset of the u^k / u^{k-1} staging area in shared memory, -1: L2
   int stage_mode;      // 1: shared-memory staging, 2: L2 prefetch (launchers set stage_off)
+  int persist;         // 1: persistent clusters loop over strips (grid set by the launcher)
 };
 
 // Launchers (adi_forward.cu).

@@ -276,6 +276,7 @@ int adi_wave::launch_fwd(Grid& G, const float* u_cur, float* u_prev, float* w, f
   xa.sc = G.dt * G.dt / (2.0 * G.hx * G.hx);
   xa.src_scale = G.dt * G.dt / (G.hx * G.hy);
   xa.gd = gd;
+  xa.persist = P.persist;
   YArgs ya;
   ya.nx = G.nx;
   ya.ny = G.ny;
@@ -290,6 +291,7 @@ int adi_wave::launch_fwd(Grid& G, const float* u_cur, float* u_prev, float* w, f
   ya.u_prev = u_prev;
   ya.z_out = z_out;
   ya.stage_mode = P.y_stage;
+  ya.persist = P.persist;
   ya.stage_off = 0;
   ya.sc = G.dt * G.dt / (2.0 * G.hy * G.hy);
   ya.gd = gd;

@@ -27,6 +27,7 @@ struct GridPlan {
   bool tree = true;  // solver variant (see adi_sweeps.cuh)
   int cta_threads = 0, cta_threads_y = 0;
   int y_stage = 1;   // 1: shared-memory staging, 2: L2 prefetch
+  int persist = 0;   // 1: persistent sweeps with L2 prefetch of the next tile
 };
 
 struct Grid {
@@ -89,7 +90,7 @@ struct adi_wave {
   int rec_cap = 0;
   cudaStream_t cap = nullptr;  // private stream used only for graph capture
   cudaGraphExec_t pair[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [orientation][gather]
-  adi_wave_tuning tuning = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  adi_wave_tuning tuning = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   int ckpt_every = 0;
   adi::RunRecord rr;
   adi::AdjWork aw;
