@@ -80,7 +80,9 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
     const int tsys = next_pow2((G.nx + K - 1) / K);
     if (tsys > maxT) { why = "nx too large for one CTA per row"; return ADI_EUNSUPPORTED; }
     int spc = t.rows_per_cta;
-    if (spc == 0) spc = std::max(1, std::min(maxT / tsys, G.ny / 304));
+    // default: about 256 threads per CTA (one row per CTA once a row needs
+    // more), at least two CTAs per SM when the grid has the rows for it
+    if (spc == 0) spc = std::max(1, std::min(std::min(maxT, 256) / tsys, G.ny / 304));
     if (spc < 1 || spc * tsys > maxT) { why = "rows_per_cta too large"; return ADI_EINVAL; }
     // whole warps only: the interface solve uses full-warp shuffles
     if (tsys < 32) {
@@ -97,11 +99,12 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
   {
     const int maxT = std::min(P.fp64y ? 512 : 1024, cty ? cty : 1024);
     const int maxC = 16;
-    int W = t.cols_per_cta ? t.cols_per_cta : 8;
+    int W = t.cols_per_cta ? t.cols_per_cta : (G.nx >= 1024 && G.ny >= 1024 ? 16 : 8);
     if (W != 4 && W != 8 && W != 16 && W != 32) { why = "cols_per_cta must be 4, 8, 16 or 32"; return ADI_EINVAL; }
+    int ymaxT = maxT;
     auto geom = [&](int K, int& tcol, int& C) {
       const int ttot = next_pow2((G.ny + K - 1) / K);
-      tcol = std::min(ttot, maxT / W);
+      tcol = std::min(ttot, ymaxT / W);
       if (W * tcol < 32) tcol = 32 / W;  // whole warps; extra chunks are empty rows
       C = std::max(1, ttot / tcol);
     };
@@ -123,6 +126,21 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
         K *= 2;
       }
     }
+    // FP32, long columns, CTA size not given: 32 rows per thread in CTAs of
+    // 256 threads (two per SM) when the column fits a portable cluster of
+    // them, else 512 (one per SM, up to 16 CTAs per cluster)
+    if (cty == 0 && t.chunk_y == 0 && !P.fp64y && G.ny >= 1024) {
+      const int ttot = next_pow2((G.ny + 31) / 32);
+      const int tc256 = std::max(1, 256 / W), tc512 = std::max(1, 512 / W);
+      int tcol = 0;
+      if (ttot <= 8 * tc256) tcol = std::min(ttot, tc256);
+      else if (ttot <= maxC * tc512) tcol = tc512;
+      const int groups = tcol ? (ttot / tcol) * std::max(1, tcol / 32) : 0;
+      if (tcol && (!P.tree || groups <= 32)) {
+        K = 32;
+        ymaxT = W * tcol;
+      }
+    }
     if (K != 4 && K != 8 && K != 16 && K != 32) { why = "chunk_y must be 4, 8, 16 or 32"; return ADI_EINVAL; }
     int tcol, C;
     geom(K, tcol, C);
@@ -133,7 +151,9 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
     int stage = t.y_stage;
     if (stage == ADI_STAGE_AUTO) {
       // shared-memory staging unless it would keep a second CTA off the SM
-      const int by_regs = std::max(1, 65536 / (64 * W * tcol));
+      // (kernels of <= 512 threads with K >= 16 take up to 128 registers)
+      const int regs = (K >= 16 && W * tcol <= 512) ? 128 : 64;
+      const int by_regs = std::max(1, 65536 / (regs * W * tcol));
       const size_t per_sm = 228 * 1024;
       stage = (std::min(by_regs, 2) * (ysm + ystage + 1024) <= per_sm) ? ADI_STAGE_SMEM : ADI_STAGE_L2;
     }

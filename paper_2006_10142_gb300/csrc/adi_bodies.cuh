@@ -85,35 +85,41 @@ __device__ __forceinline__ void x_rows_body(const XArgs& a, int blk, unsigned ch
   if (active) store_vec<K, T>(a.w + row + i0, d);
 }
 
-// L2 prefetch of the rows of block `blk` (u^k and m; the halo rows of a block
-// are the neighbouring blocks' own rows).  One instruction per thread chunk.
-template <int K>
+// One bulk L2 prefetch (TMA unit): `bytes` from `p`, both multiples of 16.
+__device__ __forceinline__ void l2_prefetch_bulk(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// L2 prefetch of what block `blk` reads: rows blk*spc-1 .. blk*spc+spc of
+// u^k (the halo rows included) and rows blk*spc .. blk*spc+spc-1 of m, one
+// bulk request per row.  Rows start on 128-byte boundaries (ld is a multiple
+// of 32) and the request is nx*4 bytes rounded up to 16, inside the row pitch.
 __device__ __forceinline__ void x_prefetch_rows(const XArgs& a, int blk) {
-  const int tsys = 1 << a.log2tsys;
-  const int sys = threadIdx.x >> a.log2tsys;
-  const int i0 = (threadIdx.x & (tsys - 1)) * K;
-  const int j = blk * a.spc + sys;
-  if (j < a.ny && i0 < a.nx) {
-    const size_t off = (size_t)j * a.ld + i0;
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.u + off));
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.m + off));
+  const int nu = a.spc + 2;
+  const uint32_t bytes = (uint32_t)((a.nx * 4 + 15) & ~15);
+  for (int r = threadIdx.x; r < nu + a.spc; r += blockDim.x) {
+    const bool isu = r < nu;
+    const int j = isu ? blk * a.spc - 1 + r : blk * a.spc + (r - nu);
+    if (j >= 0 && j < a.ny) l2_prefetch_bulk((isu ? a.u : a.m) + (size_t)j * a.ld, bytes);
   }
 }
 
-// L2 prefetch of this CTA's rows of strip `strip` (w, m, u^k, u^{k-1}): the
-// threads of columns 0..3 take one field each, one instruction per row.
-template <int K>
-__device__ __forceinline__ void y_prefetch_strip(const YArgs& a, int strip, int rank) {
+// L2 prefetch of this CTA's rows of strip `strip` (w, m, u^k, u^{k-1}): one
+// bulk request of W*4 bytes per row and field.  The strip lies inside the row
+// pitch (ld is a multiple of 32 >= W), so every request is in bounds.
+__device__ __forceinline__ void y_prefetch_strip(const YArgs& a, int strip, int rank, int K) {
+  const int log2rows = a.log2tcol + (31 - __clz(K));
+  const int rows = 1 << log2rows;
   const int W = 1 << a.log2W;
-  const int col = threadIdx.x & (W - 1);
-  if (col >= 4) return;
-  const int q = threadIdx.x >> a.log2W;
-  const int j0 = (rank * (1 << a.log2tcol) + q) * K;
-  const float* f = col == 0 ? a.w : col == 1 ? a.m : col == 2 ? a.u_cur : a.u_prev;
-  const size_t base = (size_t)j0 * a.ld + (size_t)strip * W;
-#pragma unroll
-  for (int k = 0; k < K; ++k)
-    if (j0 + k < a.ny) asm volatile("prefetch.global.L2 [%0];" ::"l"(f + base + (size_t)k * a.ld));
+  const size_t off = (size_t)strip * W;
+  for (int t = threadIdx.x; t < 4 * rows; t += blockDim.x) {
+    const int f = t >> log2rows;
+    const int j = rank * rows + (t & (rows - 1));
+    if (j < a.ny) {
+      const float* base = f == 0 ? a.w : f == 1 ? a.m : f == 2 ? a.u_cur : a.u_prev;
+      l2_prefetch_bulk(base + (size_t)j * a.ld + off, (uint32_t)(W * 4));
+    }
+  }
 }
 
 // Strip `strip` of 2^log2W columns, cluster rank `rank` of C along the
@@ -146,12 +152,12 @@ __device__ __forceinline__ void y_strip_body(const YArgs& a, int strip, int rank
   const bool smem_stage = a.stage_off >= 0;
   float* stage = reinterpret_cast<float*>(smem + (smem_stage ? a.stage_off : 0));
   if (!smem_stage) {
-    if (col == 0) {
+    if (col == 0) {  // base is the strip's first column here; W*4 bytes stay in the pitch
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         if (j0 + k < a.ny) {
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(a.u_cur + base + k * ld));
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(a.u_prev + base + k * ld));
+          l2_prefetch_bulk(a.u_cur + base + k * ld, (uint32_t)(W * 4));
+          l2_prefetch_bulk(a.u_prev + base + k * ld, (uint32_t)(W * 4));
         }
       }
     }
@@ -189,19 +195,43 @@ __device__ __forceinline__ void y_strip_body(const YArgs& a, int strip, int rank
   y_solve_cols<K, T, TREE>(smem, a.log2W, a.log2tcol, C, rank, a.pcr, col, gq, d, s);
 
   if (smem_stage) asm volatile("cp.async.wait_all;" ::: "memory");  // this thread's staged rows
-  bool bad = false;
+  // chk accumulates un - un: zero while every new value is finite, NaN after
+  // the first Inf or NaN (no fast-math, so the difference is not folded)
+  float chk = 0.f;
+  if (full && smem_stage) {
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    if (full || (colok && (j0 + k) < a.ny)) {
+    for (int k = 0; k < K; ++k) {
+      const float un = 2.0f * stage[k * threads + tid] - stage[(K + k) * threads + tid] + (float)d[k];
+      a.u_prev[base + k * ld] = un;
+      chk += un - un;
+    }
+  } else if (full) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
       const size_t idx = base + k * ld;
-      const float uc = smem_stage ? stage[k * threads + tid] : __ldcg(a.u_cur + idx);
-      const float up = smem_stage ? stage[(K + k) * threads + tid] : __ldcg(a.u_prev + idx);
-      const float un = 2.0f * uc - up + (float)d[k];
+      const float un = 2.0f * __ldcg(a.u_cur + idx) - __ldcg(a.u_prev + idx) + (float)d[k];
       a.u_prev[idx] = un;
-      if (a.z_out) a.z_out[idx] = (float)d[k];
-      bad |= !isfinite(un);
+      chk += un - un;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (colok && (j0 + k) < a.ny) {
+        const size_t idx = base + k * ld;
+        const float uc = smem_stage ? stage[k * threads + tid] : __ldcg(a.u_cur + idx);
+        const float up = smem_stage ? stage[(K + k) * threads + tid] : __ldcg(a.u_prev + idx);
+        const float un = 2.0f * uc - up + (float)d[k];
+        a.u_prev[idx] = un;
+        chk += un - un;
+      }
     }
   }
+  if (a.z_out != nullptr && colok) {
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if ((j0 + k) < a.ny) a.z_out[base + k * ld] = (float)d[k];
+  }
+  const bool bad = chk != 0.f;
   if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0 && a.err) atomicOr(a.err, ERR_NUMERIC);
   if (bump && tid == 0 && a.gd) a.gd->k += 1;
 }

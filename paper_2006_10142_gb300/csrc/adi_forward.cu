@@ -24,8 +24,13 @@ namespace adi {
 // ---------------------------------------------------------------------------
 // pass 1: RHS assembly + x solve (adi_bodies.cuh).  CTA = `spc` rows.
 // ---------------------------------------------------------------------------
+// MAXT bounds the CTA size: 1024 caps a thread at 64 registers, 512 at 128,
+// 256 at 128 with two CTAs per SM; the launchers pick the smallest bound that
+// holds the CTA, so long chunks (K = 16, 32) keep their registers.
+constexpr int min_ctas(int maxt) { return maxt <= 256 ? 2 : 1; }
+
 template <int K, typename T, int MAXT, bool TREE>
-__global__ void __launch_bounds__(MAXT, 1) x_sweep_kernel(const XArgs a) {
+__global__ void __launch_bounds__(MAXT, min_ctas(MAXT)) x_sweep_kernel(const XArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (!a.persist) {
     x_rows_body<K, T, TREE>(a, blockIdx.x, smem);
@@ -35,7 +40,7 @@ __global__ void __launch_bounds__(MAXT, 1) x_sweep_kernel(const XArgs a) {
   // and m into L2 while this one is solved
   const int nblk = (a.ny + a.spc - 1) / a.spc;
   for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-    if (blk + (int)gridDim.x < nblk) x_prefetch_rows<K>(a, blk + gridDim.x);
+    if (blk + (int)gridDim.x < nblk) x_prefetch_rows(a, blk + gridDim.x);
     x_rows_body<K, T, TREE>(a, blk, smem);
     __syncthreads();  // shared memory is reused by the next block
   }
@@ -46,7 +51,7 @@ __global__ void __launch_bounds__(MAXT, 1) x_sweep_kernel(const XArgs a) {
 // cluster of C CTAs covers the whole column length.
 // ---------------------------------------------------------------------------
 template <int K, typename T, int MAXT, bool TREE>
-__global__ void __launch_bounds__(MAXT, 1) y_sweep_kernel(const YArgs a) {
+__global__ void __launch_bounds__(MAXT, min_ctas(MAXT)) y_sweep_kernel(const YArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int rank = cluster_rank(a.C);
   if (!a.persist) {
@@ -63,7 +68,7 @@ __global__ void __launch_bounds__(MAXT, 1) y_sweep_kernel(const YArgs a) {
   const int nclusters = gridDim.x / a.C;
   for (int strip = blockIdx.x / a.C; strip < nstrips; strip += nclusters) {
     cluster_arrive_early(a.C);
-    if (strip + nclusters < nstrips) y_prefetch_strip<K>(a, strip + nclusters, rank);
+    if (strip + nclusters < nstrips) y_prefetch_strip(a, strip + nclusters, rank, K);
     y_strip_body<K, T, TREE>(a, strip, rank, strip == 0 && rank == 0, smem);
     __syncthreads();  // shared memory is reused by the next strip
   }
@@ -213,6 +218,8 @@ static cudaError_t launch_y_t(const YArgs& a_in, cudaStream_t st) {
   return cudaLaunchKernelEx(&cfg, y_sweep_kernel<K, T, MAXT, TREE>, a);
 }
 
+// K = 4, 8 fit 64 registers; K = 16, 32 take the smallest bound that holds
+// `threads` (float only; FP64 kernels are bounded at 512).
 #define ADI_DISPATCH_K(FN, TT, MT, TR, ARGS)             \
   switch (K) {                                           \
     case 4: return FN<4, TT, MT, TR> ARGS;               \
@@ -221,24 +228,40 @@ static cudaError_t launch_y_t(const YArgs& a_in, cudaStream_t st) {
     case 32: return FN<32, TT, MT, TR> ARGS;             \
   }
 
+#define ADI_DISPATCH_KF(FN, TR, ARGS, THREADS)                       \
+  switch (K) {                                                       \
+    case 4: return FN<4, float, 1024, TR> ARGS;                      \
+    case 8: return FN<8, float, 1024, TR> ARGS;                      \
+    case 16:                                                         \
+      if ((THREADS) <= 256) return FN<16, float, 256, TR> ARGS;      \
+      if ((THREADS) <= 512) return FN<16, float, 512, TR> ARGS;      \
+      return FN<16, float, 1024, TR> ARGS;                           \
+    case 32:                                                         \
+      if ((THREADS) <= 256) return FN<32, float, 256, TR> ARGS;      \
+      if ((THREADS) <= 512) return FN<32, float, 512, TR> ARGS;      \
+      return FN<32, float, 1024, TR> ARGS;                           \
+  }
+
 cudaError_t launch_x(const XArgs& a, int K, bool fp64, bool tree, cudaStream_t st) {
+  const int threads = a.spc << a.log2tsys;
   if (fp64) {
     if (tree) { ADI_DISPATCH_K(launch_x_t, double, 512, true, (a, st)) }
     else { ADI_DISPATCH_K(launch_x_t, double, 512, false, (a, st)) }
   } else {
-    if (tree) { ADI_DISPATCH_K(launch_x_t, float, 1024, true, (a, st)) }
-    else { ADI_DISPATCH_K(launch_x_t, float, 1024, false, (a, st)) }
+    if (tree) { ADI_DISPATCH_KF(launch_x_t, true, (a, st), threads) }
+    else { ADI_DISPATCH_KF(launch_x_t, false, (a, st), threads) }
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_y(const YArgs& a, int K, bool fp64, bool tree, cudaStream_t st) {
+  const int threads = 1 << (a.log2W + a.log2tcol);
   if (fp64) {
     if (tree) { ADI_DISPATCH_K(launch_y_t, double, 512, true, (a, st)) }
     else { ADI_DISPATCH_K(launch_y_t, double, 512, false, (a, st)) }
   } else {
-    if (tree) { ADI_DISPATCH_K(launch_y_t, float, 1024, true, (a, st)) }
-    else { ADI_DISPATCH_K(launch_y_t, float, 1024, false, (a, st)) }
+    if (tree) { ADI_DISPATCH_KF(launch_y_t, true, (a, st), threads) }
+    else { ADI_DISPATCH_KF(launch_y_t, false, (a, st), threads) }
   }
   return cudaErrorInvalidValue;
 }
@@ -258,6 +281,12 @@ static cudaError_t allow_smem(KernT kern, bool cluster16) {
   if (e == cudaSuccess) e = allow_smem(KERN<16, TT, MT, TR>, CL);        \
   if (e == cudaSuccess) e = allow_smem(KERN<32, TT, MT, TR>, CL);
 
+#define ADI_CFG_SMALL(KERN, TR, CL)                                      \
+  if (e == cudaSuccess) e = allow_smem(KERN<16, float, 256, TR>, CL);    \
+  if (e == cudaSuccess) e = allow_smem(KERN<16, float, 512, TR>, CL);    \
+  if (e == cudaSuccess) e = allow_smem(KERN<32, float, 256, TR>, CL);    \
+  if (e == cudaSuccess) e = allow_smem(KERN<32, float, 512, TR>, CL);
+
 cudaError_t configure_kernels() {
   cudaError_t e = cudaSuccess;
   ADI_CFG4(x_sweep_kernel, float, 1024, true, false)
@@ -268,6 +297,10 @@ cudaError_t configure_kernels() {
   ADI_CFG4(y_sweep_kernel, float, 1024, false, true)
   ADI_CFG4(y_sweep_kernel, double, 512, true, true)
   ADI_CFG4(y_sweep_kernel, double, 512, false, true)
+  ADI_CFG_SMALL(x_sweep_kernel, true, false)
+  ADI_CFG_SMALL(x_sweep_kernel, false, false)
+  ADI_CFG_SMALL(y_sweep_kernel, true, true)
+  ADI_CFG_SMALL(y_sweep_kernel, false, true)
   return e;
 }
 

@@ -173,10 +173,12 @@ __device__ __forceinline__ void y_solve_cols(unsigned char* smem, int log2W, int
                                              int rank, int pcr, int col, int gq, T (&d)[K],
                                              T (&s)[K]) {
   const int W = 1 << log2W;
-  const int owner = col % C;
-  const int slot = col / C;
-  const int n_slots = (W + C - 1) / C;
-  const int n_own = (rank < W) ? (W - 1 - rank) / C + 1 : 0;
+  // C, W, tcol and the group counts are powers of two: shifts, not divisions
+  const int log2C = 31 - __clz(C);
+  const int owner = col & (C - 1);
+  const int slot = col >> log2C;
+  const int n_slots = (W + C - 1) >> log2C;
+  const int n_own = (rank < W) ? ((W - 1 - rank) >> log2C) + 1 : 0;
   if constexpr (TREE) {
     const int tcol = 1 << log2tcol;
     const int lane = threadIdx.x & 31;
@@ -200,13 +202,13 @@ __device__ __forceinline__ void y_solve_cols(unsigned char* smem, int log2W, int
     __syncthreads();
     // re-map: each warp reduces up to 32 consecutive chunks of one column
     const int task = warp * (32 >> lg) + (lane >> lg);  // (column, group) handled by this lane
-    const int tc = task / gpc;
-    const int tg = task % gpc;
+    const int tc = task >> (log2tcol - lg);
+    const int tg = task & (gpc - 1);
     const int chunk = tg * LG + (lane & (LG - 1));
     Seg<T> S = csum[tc * tcol + chunk];
     S = warp_tree_up<T>(S, nodes, lane, lg);
     const int gg = rank * gpc + tg;  // global group index of this lane's group
-    const int t_owner = tc % C, t_slot = tc / C;
+    const int t_owner = tc & (C - 1), t_slot = tc >> log2C;
     Seg<T>* tdst = tops + t_slot * G + gg;
     if (C > 1) {
       cgx::cluster_group cl = cgx::this_cluster();
