@@ -260,6 +260,49 @@ int adi_wave_set_wait_hook(adi_wave *h, int64_t spin_limit, int32_t never_ready_
  * kinds, graph replays counted per kernel node). */
 int64_t adi_wave_launch_count(const adi_wave *h);
 
+/* ---- one step without allocation ------------------------------------------
+ * The paper has no counterpart of this call: it is a library convenience.
+ *
+ * One time step of the factored scheme (the same x and y sweep kernels as
+ * adi_wave_step, with the plan a new handle would choose) on buffers the
+ * caller owns, with no handle and no device memory allocated by the call
+ * or by anything it calls.  It is meant for callers that cannot allocate
+ * while they step: code whose device memory is already handed out to its
+ * own pool, or a time loop that must not meet the device-wide
+ * synchronisation cudaFree implies or the latency of cudaMalloc.
+ *
+ * The x sweep's result w, the one intermediate field of a step, lives in a
+ * static device array of 4,194,304 floats (16 MiB) that the library sets
+ * aside when its module loads, so grids are limited to ld * ny <= 4194304
+ * (for example 2048 x 2048); larger grids get ADI_EINVAL and a message
+ * from adi_wave_last_error(NULL).  The array needs no initial value.
+ *
+ *   desc    host pointer; nx, ny, lx, ly, dt, fp64_solve as for
+ *           adi_wave_init (start is ignored).
+ *   ld      row pitch in floats of m, u_cur and u_prev: a multiple of 32,
+ *           >= nx.  Unlike the rest of this ABI these fields are PITCHED,
+ *           [ny][ld], and their padding columns nx..ld-1 must hold zeros
+ *           (the sweeps read them as the Dirichlet ring's values).
+ *   m_max   the largest value of m; picks FP32 or FP64 elimination as
+ *           ADI_FP64_AUTO does (it must be > 0).
+ *   m       device [ny][ld] coefficient m = c^2 > 0.
+ *   u_cur   device [ny][ld] u^k, read only.
+ *   u_prev  device [ny][ld] u^{k-1} on entry, u^{k+1} on completion.
+ *   src     host pointer to the point source or NULL; wavelet[k] is used.
+ *   k       time level of u_cur (>= 0).
+ * Buffers must be 16-byte aligned and u_cur != u_prev.  Non-finite values
+ * are not reported by this call.
+ *
+ * The first call on a device looks up the static array's address and sets
+ * kernel attributes; make that first call before any stream capture that
+ * should contain later calls.  The static array is shared by all calls on
+ * a device: two calls whose work overlaps in time (different streams
+ * without an event between them, or several host threads) race on it and
+ * give wrong results.  Order them on one stream. */
+int adi_wave_step_noalloc(const adi_wave_desc *desc, int32_t ld, double m_max,
+                          const float *m, const float *u_cur, float *u_prev,
+                          const adi_source *src, int64_t k, void *stream);
+
 /* Library version string, e.g. "adiwave 0.1 sm_103a". */
 const char *adi_wave_version(void);
 

@@ -42,6 +42,7 @@ EXPORTS = (
     "adi_wave_destroy", "adi_wave_strerror", "adi_wave_last_error", "adi_wave_get_tuning",
     "adi_wave_set_tuning", "adi_wave_profile", "adi_wave_profile_read", "adi_wave_launch_count",
     "adi_wave_version", "adi_wave_set_batch_mode", "adi_wave_set_wait_hook",
+    "adi_wave_step_noalloc",
 )
 
 
@@ -122,6 +123,8 @@ def load(build_if_missing: bool = True):
         lib.adi_wave_version.restype = ctypes.c_char_p
         lib.adi_wave_set_batch_mode.argtypes = [P, i32]
         lib.adi_wave_set_wait_hook.argtypes = [P, i64, i32]
+        lib.adi_wave_step_noalloc.argtypes = [ctypes.POINTER(Desc), i32, ctypes.c_double, P, P, P,
+                                              ctypes.POINTER(Source), i64, P]
         for name in EXPORTS:
             if not hasattr(lib, name):
                 raise RuntimeError("libadiwave.so does not export %s" % name)

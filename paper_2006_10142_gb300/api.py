@@ -320,5 +320,40 @@ class AdiWaveBatch:
         return int(self._lib.adi_wave_launch_count(self._h))
 
 
+def step_noalloc(m: torch.Tensor, u_cur: torch.Tensor, u_prev: torch.Tensor, nx: int, dt: float,
+                 m_max: float, k: int, lx: float = 1.0, ly: float = 1.0, fp64: str = "auto",
+                 src: Optional[Tuple[int, int]] = None, wavelet: Optional[torch.Tensor] = None,
+                 stream=None):
+    """adi_wave_step_noalloc: one step on caller-owned PITCHED buffers.
+
+    m, u_cur, u_prev are contiguous float32 CUDA tensors of shape [ny, ld]
+    (ld a multiple of 32, >= nx, padding columns zero); u_prev is overwritten
+    with u^{k+1}.  Neither this function nor the library call allocates
+    device memory: the tensors are passed as they are (no copies), and the
+    x sweep's intermediate lives in the library's fixed static array, which
+    limits ld * ny to 4194304.  Calls on one device must not overlap.
+    """
+    lib = _lib.load()
+    ny, ld = u_cur.shape
+    for name, t in (("m", m), ("u_cur", u_cur), ("u_prev", u_prev)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32):
+            raise TypeError("%s must be a float32 CUDA tensor" % name)
+        if tuple(t.shape) != (ny, ld) or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous [%d, %d] tensor" % (name, ny, ld))
+    srcs = None
+    if src is not None:
+        if wavelet is None or not wavelet.is_cuda or wavelet.dtype != torch.float32 \
+                or not wavelet.is_contiguous():
+            raise ValueError("a source needs contiguous float32 CUDA wavelet samples")
+        srcs = Source(int(src[0]), int(src[1]), wavelet.data_ptr(), int(wavelet.numel()))
+    desc = Desc(int(nx), int(ny), float(lx), float(ly), float(dt), 0, _FP64[fp64])
+    with torch.cuda.device(u_cur.device):
+        rc = lib.adi_wave_step_noalloc(ctypes.byref(desc), int(ld), float(m_max), _ptr(m),
+                                       _ptr(u_cur), _ptr(u_prev),
+                                       ctypes.byref(srcs) if srcs is not None else None, int(k),
+                                       _stream_ptr(stream))
+    _lib.check(rc, None, "adi_wave_step_noalloc")
+
+
 def version() -> str:
     return _lib.load().adi_wave_version().decode()

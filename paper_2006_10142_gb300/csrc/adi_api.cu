@@ -201,6 +201,9 @@ extern "C" const char* adi_wave_strerror(int code) {
 // Detail of the last adi_wave_init failure on this thread (the handle is gone).
 static thread_local std::string g_init_error;
 
+// Detail of a failed handle-less call, reported by adi_wave_last_error(NULL).
+void adi::set_thread_error(const std::string& msg) { g_init_error = msg; }
+
 extern "C" const char* adi_wave_last_error(const adi_wave* h) {
   return h ? h->err.c_str() : g_init_error.c_str();
 }

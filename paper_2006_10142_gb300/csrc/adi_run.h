@@ -148,4 +148,5 @@ namespace adi {
 int fail(adi_wave* h, int code, const std::string& msg);
 int cuda_fail(adi_wave* h, cudaError_t e, const char* what);
 int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why);
+void set_thread_error(const std::string& msg);
 }  // namespace adi
