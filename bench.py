@@ -52,10 +52,11 @@ UNIT = "grid-point updates/s"
 # algorithmic HBM bytes per grid point per launch (FP32 fields)
 BYTES_X = 12  # read u^k, m; write w
 BYTES_Y = 20  # read w, m, u^k, u^{k-1}; write u^{k+1}
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
-# kernel from the ncu capture summarised in profiles/ (absent until measured
-# for the current kernels)
-NCU_TRAFFIC = {}
+# dram__bytes_read.sum + dram__bytes_write.sum per 16384^2 launch of the
+# dominant kernel: measured by ncu on a 4096 x 16384 grid with the same launch
+# shape (profiles/y_sweep_kernel_4096x16384.txt) and scaled by the number of
+# grid points (x 4).  Only valid for the 16384^2 workload.
+NCU_TRAFFIC = {("ricker_16384", "y_sweep_kernel"): 5277511680}
 
 
 def measured_peak_gbs():
@@ -295,7 +296,7 @@ def _max_over_ranks(ctx, v):
     return float(t.item())
 
 
-def _roofline(kms, kcnt, kinds, alg_bytes):
+def _roofline(kms, kcnt, kinds, alg_bytes, workload=None):
     """Dominant kernel's algorithmic GB/s against the measured copy bandwidth."""
     peak, peak_kind = measured_peak_gbs()
     k = max(kinds, key=lambda q: kms[q])
@@ -303,7 +304,7 @@ def _roofline(kms, kcnt, kinds, alg_bytes):
     achieved = alg_bytes[k] / (per_launch_ms / 1e3) / 1e9
     return {"bound": "hbm", "kernel": kinds[k], "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-            "traffic": NCU_TRAFFIC.get(kinds[k]), "alg_bytes_per_launch": alg_bytes[k],
+            "traffic": NCU_TRAFFIC.get((workload, kinds[k])), "alg_bytes_per_launch": alg_bytes[k],
             "avg_launch_ms": per_launch_ms,
             "kernel_ms": {kinds[q]: kms[q] for q in kinds},
             "kernel_launches": {kinds[q]: kcnt[q] for q in kinds}}
@@ -339,7 +340,7 @@ def run_single(ctx):
     h.sync_status()
     value = world * n * n * ts * args.steps / (max_ms / 1e3)
     roof = _roofline(kms, kcnt, {0: "x_sweep_kernel", 1: "y_sweep_kernel"},
-                     {0: BYTES_X * n * n, 1: BYTES_Y * n * n})
+                     {0: BYTES_X * n * n, 1: BYTES_Y * n * n}, args.workload)
     roof["step_gbs_32B"] = 32.0 * n * n * ts * args.steps / (max_ms / 1e3) / 1e9
 
     e2e = None
