@@ -203,13 +203,27 @@ const char *adi_wave_last_error(const adi_wave *h);
  * cta_threads_y:    the same for the y sweep;
  * y_stage:          how the y sweep fetches u^k, u^{k-1} for its update while
  *                   it solves: ADI_STAGE_SMEM (asynchronous copies into
- *                   shared memory) or ADI_STAGE_L2 (prefetch into L2, no
- *                   shared memory, more CTAs per SM);
+ *                   shared memory), ADI_STAGE_L2 (prefetch into L2, no
+ *                   shared memory, more CTAs per SM) or ADI_STAGE_TMA
+ *                   (persistent clusters: the next strip's w and m arrive in
+ *                   shared memory by bulk asynchronous copies while the
+ *                   current strip is solved, and its u^k, u^{k-1} are
+ *                   prefetched into L2; FP32 tree solver, 16 columns);
  * persist:          1 = one wave of resident CTAs (clusters) loops over the
  *                   tiles of each sweep and prefetches its next tile into L2
- *                   while solving the current one; -1 = one CTA per tile.
+ *                   while solving the current one; -1 = one CTA per tile;
+ * x_stage:          how the x sweep reads its rows: ADI_STAGE_SMEM (coalesced
+ *                   loads, right-hand side formed in that layout and handed
+ *                   to the solving threads through shared memory; w written
+ *                   back the same way) or ADI_STAGE_DIRECT (each thread loads
+ *                   and stores its own chunk) or ADI_STAGE_TMA (persistent
+ *                   CTAs; the next rows of u^k and m arrive in shared memory
+ *                   by TMA tensor copies while the current rows are solved;
+ *                   FP32 tree solver, rows of >= 256 floats); FP64
+ *                   elimination always reads directly.
  * Zero fields mean "choose automatically". */
-enum { ADI_STAGE_AUTO = 0, ADI_STAGE_SMEM = 1, ADI_STAGE_L2 = 2 };
+enum { ADI_STAGE_AUTO = 0, ADI_STAGE_SMEM = 1, ADI_STAGE_L2 = 2, ADI_STAGE_DIRECT = 2,
+       ADI_STAGE_TMA = 3 };
 enum { ADI_SOLVER_AUTO = 0, ADI_SOLVER_TREE = 1, ADI_SOLVER_CR_SMEM = 2 };
 typedef struct {
     int32_t chunk_x, chunk_y;
@@ -222,6 +236,7 @@ typedef struct {
     int32_t cta_threads_y;
     int32_t y_stage;
     int32_t persist;
+    int32_t x_stage;
 } adi_wave_tuning;
 
 int adi_wave_get_tuning(const adi_wave *h, adi_wave_tuning *t);

@@ -91,6 +91,23 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
       if (spc * tsys > maxT) spc = maxT / tsys;
     }
     if (x_smem_bytes(spc, tsys, P.fp64x, P.tree) > (size_t)kMaxDynSmem) { why = "x sweep shared memory too large"; return ADI_EUNSUPPORTED; }
+    if (t.x_stage < ADI_STAGE_AUTO || t.x_stage > ADI_STAGE_TMA) { why = "unknown x_stage"; return ADI_EINVAL; }
+    // TMA pipeline: FP32 tree solver, rows of >= 256 staged floats, K >= 8,
+    // K = 32 only up to 512 threads (register budget)
+    const bool pipe_ok = !P.fp64x && P.tree && tsys * K >= 256 && K >= 8 &&
+                         (K < 32 || spc * tsys <= 512) &&
+                         x_pipe_smem_bytes(spc, tsys, K) <= (size_t)kMaxDynSmem;
+    const bool smem_ok = !P.fp64x &&
+                         align64(x_smem_bytes(spc, tsys, P.fp64x, P.tree)) + x_stage_bytes(spc * tsys, K) <=
+                             (size_t)kMaxDynSmem;
+    int xs = t.x_stage;
+    if (xs == ADI_STAGE_AUTO) xs = pipe_ok ? ADI_STAGE_TMA : ADI_STAGE_DIRECT;
+    if (xs == ADI_STAGE_TMA && !pipe_ok) { why = "x TMA pipeline not available for this shape"; return ADI_EUNSUPPORTED; }
+    if (xs == ADI_STAGE_SMEM && !smem_ok) {
+      if (P.fp64x) xs = ADI_STAGE_DIRECT;
+      else { why = "x staging does not fit shared memory"; return ADI_EUNSUPPORTED; }
+    }
+    P.x_stage = xs;
     P.kx = K;
     P.log2tsys = ilog2(tsys);
     P.spc = spc;
@@ -147,8 +164,13 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
     if (!fits(K)) { why = "ny too large for this chunk_y (cluster or top system)"; return ADI_EUNSUPPORTED; }
     const size_t ysm = align64(y_smem_bytes(W, C, tcol, P.fp64y, P.tree));
     const size_t ystage = y_stage_bytes(W * tcol, K);
-    if (t.y_stage < ADI_STAGE_AUTO || t.y_stage > ADI_STAGE_L2) { why = "unknown y_stage"; return ADI_EINVAL; }
+    if (t.y_stage < ADI_STAGE_AUTO || t.y_stage > ADI_STAGE_TMA) { why = "unknown y_stage"; return ADI_EINVAL; }
     int stage = t.y_stage;
+    // pipelined strips: FP32 tree solver, 16 columns, K >= 16, <= 512 threads
+    const bool ypipe_ok = !P.fp64y && P.tree && W == 16 && K >= 16 && W * tcol <= 512 && tcol * K >= 64 &&
+                          y_pipe_smem_bytes(C, tcol, K) <= (size_t)kMaxDynSmem;
+    if (stage == ADI_STAGE_TMA && !ypipe_ok) { why = "y pipeline not available for this shape"; return ADI_EUNSUPPORTED; }
+    if (stage == ADI_STAGE_AUTO && ypipe_ok) stage = ADI_STAGE_TMA;
     if (stage == ADI_STAGE_AUTO) {
       // shared-memory staging unless it would keep a second CTA off the SM
       // (kernels of <= 512 threads with K >= 16 take up to 128 registers)
@@ -157,7 +179,7 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
       const size_t per_sm = 228 * 1024;
       stage = (std::min(by_regs, 2) * (ysm + ystage + 1024) <= per_sm) ? ADI_STAGE_SMEM : ADI_STAGE_L2;
     }
-    if (ysm + (stage == ADI_STAGE_SMEM ? ystage : 0) > (size_t)kMaxDynSmem) {
+    if (stage != ADI_STAGE_TMA && ysm + (stage == ADI_STAGE_SMEM ? ystage : 0) > (size_t)kMaxDynSmem) {
       why = "y sweep shared memory too large";
       return ADI_EUNSUPPORTED;
     }
@@ -312,6 +334,7 @@ extern "C" int adi_wave_get_tuning(const adi_wave* h, adi_wave_tuning* t) {
   t->cta_threads_y = P.cta_threads_y;
   t->y_stage = P.y_stage;
   t->persist = P.persist ? 1 : -1;
+  t->x_stage = P.x_stage;
   return ADI_OK;
 }
 

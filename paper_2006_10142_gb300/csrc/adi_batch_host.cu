@@ -69,6 +69,9 @@ int adi_wave::setup_batch(cudaStream_t st) {
       xa.src_scale = G.dt * G.dt / (G.hx * G.hy);
       xa.gd = G.gd;
       xa.persist = 0;
+      xa.stage_mode = 2;
+      xa.stage_off = -1;
+      xa.err = nullptr;
       YArgs& ya = B.ya[c];
       ya.nx = G.nx; ya.ny = G.ny; ya.ld = G.ld;
       ya.log2W = ilog2(W); ya.log2tcol = ilog2(tcol); ya.C = 1; ya.pcr = 32;

@@ -85,6 +85,116 @@ __device__ __forceinline__ void x_rows_body(const XArgs& a, int blk, unsigned ch
   if (active) store_vec<K, T>(a.w + row + i0, d);
 }
 
+// Staged form of x_rows_body (FP32): the CTA's rows are read with coalesced
+// float4 loads (consecutive lanes, consecutive 16-byte groups), the
+// right-hand side r = tau^2 (m Lap u^k + f^k) and s = sc m are formed in
+// that layout -- horizontal neighbours come from the adjacent lanes by
+// shuffle -- and handed to the solving threads through shared memory; the
+// solution w goes back the same way and is stored coalesced.  Shared memory
+// at `stage` holds [2][threads*K/4] float4 slots (r or w, then s) in the
+// swizzled order of swz4(), so both access patterns are conflict-free.
+// The arithmetic is that of x_rows_body, term for term.
+
+// Slot of logical float4 index f: the 16-byte slot within each 128-byte
+// row is XOR-ed with the row index.  Eight consecutive f (coalesced) and
+// f = t*K/4 + c for eight consecutive t (a thread's chunk) both land in
+// eight distinct slots of a 128-byte row.
+__device__ __forceinline__ int swz4(int f) { return f ^ ((f >> 3) & 7); }
+
+template <int K, bool TREE>
+__device__ __forceinline__ void x_rows_body_staged(const XArgs& a, int blk, unsigned char* smem) {
+  constexpr int NQ = K / 4;  // float4 groups per thread
+  const int threads = blockDim.x;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int log2row = a.log2tsys + (31 - __clz(K));  // elements per CTA row = tsys * K
+  const int rowlen = 1 << log2row;
+  float4* sd = reinterpret_cast<float4*>(smem + a.stage_off);
+  float4* ss = sd + threads * NQ;
+  const float cx = (float)a.cx, cy = (float)a.cy, sc = (float)a.sc;
+  const GridDev* gd = a.gd;
+  const int sx = gd->src_ix, sy = gd->src_iy;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int f = q * threads + tid;
+    const int e = f << 2;
+    const int col = e & (rowlen - 1);
+    const int j = blk * a.spc + (e >> log2row);
+    const bool ok = j < a.ny && col < a.nx;
+    const size_t row = (size_t)j * a.ld;
+    float4 c4 = z4, m4 = z4, v4 = z4, w4 = z4;
+    if (ok) {
+      c4 = __ldg(reinterpret_cast<const float4*>(a.u + row + col));
+      m4 = __ldg(reinterpret_cast<const float4*>(a.m + row + col));
+      if (j > 0) v4 = __ldg(reinterpret_cast<const float4*>(a.u + row - a.ld + col));
+      if (j + 1 < a.ny) w4 = __ldg(reinterpret_cast<const float4*>(a.u + row + a.ld + col));
+    }
+    // u at col - 1 and col + 4: the neighbouring lanes' groups (same row
+    // whenever the node exists), loaded at the warp's two ends
+    float uL = __shfl_up_sync(0xffffffffu, c4.w, 1);
+    float uR = __shfl_down_sync(0xffffffffu, c4.x, 1);
+    if (lane == 0) uL = (ok && col > 0) ? __ldg(a.u + row + col - 1) : 0.f;
+    if (lane == 31) uR = (ok && col + 4 < a.nx) ? __ldg(a.u + row + col + 4) : 0.f;
+    if (col == 0) uL = 0.f;
+    if (col + 4 >= a.nx) uR = 0.f;
+    const float uc[4] = {c4.x, c4.y, c4.z, c4.w};
+    const float mv[4] = {m4.x, m4.y, m4.z, m4.w};
+    const float vs[4] = {v4.x + w4.x, v4.y + w4.y, v4.z + w4.z, v4.w + w4.w};
+    float d[4], s[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float c = uc[k];
+      const float l = k > 0 ? uc[k - 1] : uL;
+      const float r = k < 3 ? uc[k + 1] : uR;
+      const float lap = cx * (l + r - 2.f * c) + cy * (vs[k] - 2.f * c);
+      d[k] = mv[k] * lap;
+      s[k] = sc * mv[k];
+    }
+    // point source f^k = w(t_k) / (h1 h2) at one node
+    if (ok && j == sy && sx >= col && sx < col + 4) {
+      const long long lev = gd->k;
+      if (gd->wavelet != nullptr && lev >= 0 && lev < gd->n_wavelet) {
+        const float fs = (float)a.src_scale * gd->wavelet[lev];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (col + k == sx) d[k] += fs;
+      }
+    }
+    sd[swz4(f)] = make_float4(d[0], d[1], d[2], d[3]);
+    ss[swz4(f)] = make_float4(s[0], s[1], s[2], s[3]);
+  }
+  __syncthreads();
+
+  float d[K], s[K];
+#pragma unroll
+  for (int c = 0; c < NQ; ++c) {
+    const float4 dv = sd[swz4(tid * NQ + c)];
+    const float4 sv = ss[swz4(tid * NQ + c)];
+    d[4 * c + 0] = dv.x; d[4 * c + 1] = dv.y; d[4 * c + 2] = dv.z; d[4 * c + 3] = dv.w;
+    s[4 * c + 0] = sv.x; s[4 * c + 1] = sv.y; s[4 * c + 2] = sv.z; s[4 * c + 3] = sv.w;
+  }
+  const int sys = tid >> a.log2tsys;
+  const int p = tid & ((1 << a.log2tsys) - 1);
+  x_solve_rows<K, float, TREE>(smem, a.spc, a.log2tsys, a.pcr, sys, p, d, s);
+
+  // w: each thread rewrites its own slots, then the CTA stores coalesced
+#pragma unroll
+  for (int c = 0; c < NQ; ++c)
+    sd[swz4(tid * NQ + c)] = make_float4(d[4 * c + 0], d[4 * c + 1], d[4 * c + 2], d[4 * c + 3]);
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int f = q * threads + tid;
+    const int e = f << 2;
+    const int col = e & (rowlen - 1);
+    const int j = blk * a.spc + (e >> log2row);
+    if (j < a.ny && col < a.nx)
+      *reinterpret_cast<float4*>(a.w + (size_t)j * a.ld + col) = sd[swz4(f)];
+  }
+}
+
 // One bulk L2 prefetch (TMA unit): `bytes` from `p`, both multiples of 16.
 __device__ __forceinline__ void l2_prefetch_bulk(const void* p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");

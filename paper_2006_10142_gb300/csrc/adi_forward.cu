@@ -18,6 +18,7 @@
 #include "adi_device.cuh"
 #include "adi_internal.h"
 #include "adi_sweeps.cuh"
+#include "adi_tma.cuh"
 
 namespace adi {
 
@@ -32,6 +33,21 @@ constexpr int min_ctas(int maxt) { return maxt <= 256 ? 2 : 1; }
 template <int K, typename T, int MAXT, bool TREE>
 __global__ void __launch_bounds__(MAXT, min_ctas(MAXT)) x_sweep_kernel(const XArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
+  if constexpr (sizeof(T) == 4) {
+    if (a.stage_off >= 0) {
+      if (!a.persist) {
+        x_rows_body_staged<K, TREE>(a, blockIdx.x, smem);
+        return;
+      }
+      const int nblk = (a.ny + a.spc - 1) / a.spc;
+      for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+        if (blk + (int)gridDim.x < nblk) x_prefetch_rows(a, blk + gridDim.x);
+        x_rows_body_staged<K, TREE>(a, blk, smem);
+        __syncthreads();  // shared memory is reused by the next block
+      }
+      return;
+    }
+  }
   if (!a.persist) {
     x_rows_body<K, T, TREE>(a, blockIdx.x, smem);
     return;
@@ -44,6 +60,145 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT)) x_sweep_kernel(const XAr
     x_rows_body<K, T, TREE>(a, blk, smem);
     __syncthreads();  // shared memory is reused by the next block
   }
+}
+
+// ---------------------------------------------------------------------------
+// pass 1, pipelined form (FP32, tree solver): persistent CTAs loop over row
+// blocks; while the rows of one block are solved, TMA brings the next
+// block's rows of u^k and m into shared memory, so the loads of the next
+// block overlap the solve of this one.  Halo rows come from the stage when
+// they belong to the block and from L2 otherwise (the neighbouring blocks
+// are staged by the neighbouring CTAs at about the same time; the two rows
+// just outside the next block are also prefetched into L2).
+//
+// Shared memory: [solver region] [mbarrier at a.stage_off] [pad to 1024 B]
+// [u rows: spc x rowf floats] [m rows: spc x rowf floats], rowf = tsys * K,
+// every row 1024-byte aligned in the 128-byte-swizzled layout of swz4().
+// ---------------------------------------------------------------------------
+template <int K>
+__device__ __forceinline__ void stage_vec(float (&v)[K], const float* row, int i0) {
+  const float4* r4 = reinterpret_cast<const float4*>(row);
+#pragma unroll
+  for (int c = 0; c < K / 4; ++c) {
+    const float4 t = r4[swz4((i0 >> 2) + c)];
+    v[4 * c + 0] = t.x; v[4 * c + 1] = t.y; v[4 * c + 2] = t.z; v[4 * c + 3] = t.w;
+  }
+}
+__device__ __forceinline__ float stage_at(const float* row, int e) {
+  return row[(swz4(e >> 2) << 2) | (e & 3)];
+}
+
+template <int K, int MAXT>
+__global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
+    x_pipe_kernel(const XArgs a, const __grid_constant__ CUtensorMap tm_u,
+                  const __grid_constant__ CUtensorMap tm_m) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tid = threadIdx.x;
+  const int tsys = 1 << a.log2tsys;
+  const int rowf = tsys * K;               // floats per staged row (a power of two >= 256)
+  const int lines = rowf >> 5;             // 128-byte lines per staged row
+  const int L = lines < 256 ? lines : 256; // lines per TMA box
+  const int nchunk = lines / L;
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  const uint32_t bar = sa + (uint32_t)a.stage_off;
+  const uint32_t st_u = (bar + 8u + 1023u) & ~1023u;
+  const uint32_t st_m = st_u + (uint32_t)(a.spc * rowf * 4);
+  const float* su = reinterpret_cast<const float*>(smem + (st_u - sa));
+  const float* sm = su + (size_t)a.spc * rowf;
+  const int nblk = (a.ny + a.spc - 1) / a.spc;
+  const uint32_t pf_bytes = (uint32_t)((a.nx * 4 + 15) & ~15);
+
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  // thread 0: announce and start the copies of block `blk`
+  auto issue = [&](int blk) {
+    const int j0 = blk * a.spc;
+    const int nrows = min(a.spc, a.ny - j0);
+    mbar_arrive_expect_tx(bar, (uint32_t)(2 * nrows * rowf * 4));
+    for (int r = 0; r < nrows; ++r)
+      for (int c = 0; c < nchunk; ++c) {
+        const uint32_t off = (uint32_t)((r * rowf + c * L * 32) * 4);
+        tma_load_3d(st_u + off, &tm_u, 0, c * L, j0 + r, bar);
+        tma_load_3d(st_m + off, &tm_m, 0, c * L, j0 + r, bar);
+      }
+  };
+  if (tid == 0 && (int)blockIdx.x < nblk) issue(blockIdx.x);
+
+  const int sys = tid >> a.log2tsys;
+  const int p = tid & (tsys - 1);
+  const int i0 = p * K;
+  uint32_t phase = 0;
+  bool timed_out = false;
+  for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    if (!mbar_wait_bounded(bar, phase, 1000000000ull)) timed_out = true;
+    phase ^= 1u;
+    const int j = blk * a.spc + sys;
+    const bool active = j < a.ny && i0 < a.nx;
+    float d[K], s[K];
+    if (active) {
+      const float cx = (float)a.cx, cy = (float)a.cy, sc = (float)a.sc;
+      const float* ur = su + (size_t)sys * rowf;
+      const float* mr = sm + (size_t)sys * rowf;
+      float uc[K], v[K];
+      if (sys > 0) {
+        stage_vec<K>(d, ur - rowf, i0);
+      } else if (j > 0) {
+        load_vec<K>(d, a.u + (size_t)(j - 1) * a.ld + i0);
+      } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) d[k] = 0.f;
+      }
+      if (j + 1 < a.ny) {
+        if (sys + 1 < a.spc) stage_vec<K>(v, ur + rowf, i0);
+        else load_vec<K>(v, a.u + (size_t)(j + 1) * a.ld + i0);
+#pragma unroll
+        for (int k = 0; k < K; ++k) d[k] += v[k];
+      }
+      stage_vec<K>(uc, ur, i0);
+      stage_vec<K>(v, mr, i0);
+      const float uL = (i0 > 0) ? stage_at(ur, i0 - 1) : 0.f;
+      const float uR = (i0 + K < a.nx) ? stage_at(ur, i0 + K) : 0.f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const float c = uc[k];
+        const float l = k > 0 ? uc[k - 1] : uL;
+        const float r = k < K - 1 ? uc[k + 1] : uR;
+        const float lap = cx * (l + r - 2.f * c) + cy * (d[k] - 2.f * c);
+        d[k] = v[k] * lap;
+        s[k] = sc * v[k];
+      }
+      // point source f^k = w(t_k) / (h1 h2) at one node
+      const GridDev* gd = a.gd;
+      const int sx = gd->src_ix;
+      if (j == gd->src_iy && sx >= i0 && sx < i0 + K) {
+        const long long lev = gd->k;
+        if (gd->wavelet != nullptr && lev >= 0 && lev < gd->n_wavelet) {
+          const float f = (float)a.src_scale * gd->wavelet[lev];
+#pragma unroll
+          for (int k = 0; k < K; ++k)
+            if (i0 + k == sx) d[k] += f;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < K; ++k) { d[k] = 0.f; s[k] = 0.f; }
+    }
+    __syncthreads();  // every read of the stage is done: it may be refilled
+    const int next = blk + (int)gridDim.x;
+    if (tid == 0 && next < nblk) {
+      fence_proxy_async_smem();
+      issue(next);
+      const int jl = next * a.spc - 1, jh = next * a.spc + a.spc;
+      if (jl >= 0) l2_prefetch_bulk(a.u + (size_t)jl * a.ld, pf_bytes);
+      if (jh < a.ny) l2_prefetch_bulk(a.u + (size_t)jh * a.ld, pf_bytes);
+    }
+    x_solve_rows<K, float, true>(smem, a.spc, a.log2tsys, a.pcr, sys, p, d, s);
+    if (active) store_vec<K, float>(a.w + (size_t)j * a.ld + i0, d);
+  }
+  if (timed_out && (tid & 31) == 0 && a.err) atomicOr(a.err, ERR_TIMEOUT);
 }
 
 // ---------------------------------------------------------------------------
@@ -72,6 +227,132 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT)) y_sweep_kernel(const YAr
     y_strip_body<K, T, TREE>(a, strip, rank, strip == 0 && rank == 0, smem);
     __syncthreads();  // shared memory is reused by the next strip
   }
+}
+
+// ---------------------------------------------------------------------------
+// pass 2, pipelined form (FP32, tree solver, strips of 16 columns):
+// persistent clusters loop over strips; while one strip is solved, each CTA
+// loads its rows of the next strip's w and m into shared memory with TMA
+// tensor boxes of 16 columns x BH rows (completing on an mbarrier) and
+// prefetches the same boxes of u^k and u^{k-1} into L2 for the update.
+// Shared memory: [solver region] [mbarrier at a.stage_off] [pad to 128 B]
+// [w tile] [m tile], each R x 16 floats, R = tcol * K rows of this CTA.
+// Rows beyond ny and columns beyond the row pitch arrive as zeros; columns
+// beyond nx are masked.
+// ---------------------------------------------------------------------------
+template <int K, int MAXT>
+__global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
+    y_pipe_kernel(const YArgs a, const __grid_constant__ CUtensorMap tm_w,
+                  const __grid_constant__ CUtensorMap tm_m, const __grid_constant__ CUtensorMap tm_uc,
+                  const __grid_constant__ CUtensorMap tm_up) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int W = 16;
+  const int C = a.C;
+  const int rank = cluster_rank(C);
+  const int tid = threadIdx.x;
+  const int tcol = 1 << a.log2tcol;
+  const int R = tcol * K;              // rows of this CTA's tile (a power of two >= 64)
+  const int BH = R < 256 ? R : 256;    // rows per TMA box
+  const int nbox = R / BH;
+  const int row0 = rank * R;
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  const uint32_t bar = sa + (uint32_t)a.stage_off;
+  const uint32_t st_w = (bar + 8u + 127u) & ~127u;
+  const uint32_t st_m = st_w + (uint32_t)(R * W * 4);
+  const float* sw = reinterpret_cast<const float*>(smem + (st_w - sa));
+  const float* smv = reinterpret_cast<const float*>(smem + (st_m - sa));
+  const int nstrips = (a.nx + W - 1) / W;
+  const int ncl = gridDim.x / C;
+  const size_t ld = (size_t)a.ld;
+
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  // thread 0: copies of strip `st` (this CTA's rows) and L2 prefetch of its u boxes
+  auto issue = [&](int st) {
+    mbar_arrive_expect_tx(bar, (uint32_t)(2 * R * W * 4));
+    for (int b = 0; b < nbox; ++b) {
+      const uint32_t off = (uint32_t)(b * BH * W * 4);
+      tma_load_2d(st_w + off, &tm_w, st * W, row0 + b * BH, bar);
+      tma_load_2d(st_m + off, &tm_m, st * W, row0 + b * BH, bar);
+      tma_prefetch_2d(&tm_uc, st * W, row0 + b * BH);
+      tma_prefetch_2d(&tm_up, st * W, row0 + b * BH);
+    }
+  };
+  int strip = blockIdx.x / C;
+  if (tid == 0 && strip < nstrips) issue(strip);
+  const int col = tid & (W - 1);
+  const int q = tid >> 4;
+  const int gq = rank * tcol + q;
+  const int j0 = gq * K;
+  uint32_t phase = 0;
+  bool timed_out = false;
+  bool bad = false;
+  const float sc = (float)a.sc;
+  for (; strip < nstrips; strip += ncl) {
+    cluster_arrive_early(C);
+    const int i = strip * W + col;
+    const bool colok = i < a.nx;
+    if (!mbar_wait_bounded(bar, phase, 1000000000ull)) timed_out = true;
+    phase ^= 1u;
+    float d[K], s[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int o = (q * K + k) * W + col;
+      d[k] = colok ? sw[o] : 0.f;
+      s[k] = colok ? sc * smv[o] : 0.f;
+    }
+    __syncthreads();  // the stage is consumed: refill it with the next strip
+    const int next = strip + ncl;
+    if (tid == 0 && next < nstrips) {
+      fence_proxy_async_smem();
+      issue(next);
+    }
+    y_solve_cols<K, float, true>(smem, a.log2W, a.log2tcol, C, rank, a.pcr, col, gq, d, s);
+    if (colok) {
+      const size_t base = (size_t)j0 * ld + i;
+      float chk = 0.f;
+      if (j0 + K <= a.ny) {
+        // groups of 8 rows: 16 loads in flight per thread within the register budget
+#pragma unroll
+        for (int g = 0; g < K; g += 8) {
+          float uc[8], up[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            uc[k] = __ldcg(a.u_cur + base + (g + k) * ld);
+            up[k] = __ldcg(a.u_prev + base + (g + k) * ld);
+          }
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const float un = 2.0f * uc[k] - up[k] + d[g + k];
+            a.u_prev[base + (g + k) * ld] = un;
+            chk += un - un;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          if (j0 + k < a.ny) {
+            const float un = 2.0f * __ldcg(a.u_cur + base + k * ld) - __ldcg(a.u_prev + base + k * ld) + d[k];
+            a.u_prev[base + k * ld] = un;
+            chk += un - un;
+          }
+        }
+      }
+      if (a.z_out != nullptr) {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          if (j0 + k < a.ny) a.z_out[base + k * ld] = d[k];
+      }
+      bad |= chk != 0.f;
+    }
+    if (strip == 0 && rank == 0 && tid == 0 && a.gd) a.gd->k += 1;
+    __syncthreads();  // the solver's shared memory is reused by the next strip
+  }
+  if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0 && a.err) atomicOr(a.err, ERR_NUMERIC);
+  if (timed_out && (tid & 31) == 0 && a.err) atomicOr(a.err, ERR_TIMEOUT);
 }
 
 // ---------------------------------------------------------------------------
@@ -168,13 +449,66 @@ size_t y_smem_bytes(int W, int C, int tcol, bool fp64, bool tree) {
 }
 
 size_t y_stage_bytes(int threads, int K) { return align64((size_t)2 * K * threads * sizeof(float)); }
+size_t x_stage_bytes(int threads, int K) { return align64((size_t)2 * K * threads * sizeof(float)); }
+size_t x_pipe_smem_bytes(int spc, int tsys, int K) {
+  return align64(x_smem_bytes(spc, tsys, false, true)) + 8 + 1024 + (size_t)2 * spc * tsys * K * 4;
+}
+
+// Tensor map of a pitched [ny][ld] FP32 field as {32, ld/32, ny} with
+// 128-byte swizzle and boxes of {32, box_lines, 1} (one row segment).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static cudaError_t get_encode_fn(EncodeTiledFn* out) {
+  static EncodeTiledFn fn = nullptr;
+  if (fn == nullptr) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || p == nullptr) return cudaErrorNotSupported;
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  *out = fn;
+  return cudaSuccess;
+}
+
+cudaError_t encode_row_map(CUtensorMap* out, const float* base, int ld, int ny, int box_lines) {
+  EncodeTiledFn fn = nullptr;
+  cudaError_t e = get_encode_fn(&fn);
+  if (e != cudaSuccess) return e;
+  if (ld % 32 != 0 || box_lines < 1 || box_lines > 256 || ((uintptr_t)base & 15) != 0)
+    return cudaErrorInvalidValue;
+  const cuuint64_t dims[3] = {32, (cuuint64_t)(ld / 32), (cuuint64_t)ny};
+  const cuuint64_t strides[2] = {128, (cuuint64_t)ld * 4};
+  const cuuint32_t box[3] = {32, (cuuint32_t)box_lines, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims,
+                        strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+int x_pipe_box_lines(int tsys, int K) {
+  const int lines = tsys * K / 32;
+  return lines < 256 ? lines : 256;
+}
 
 template <int K, typename T, int MAXT, bool TREE>
-static cudaError_t launch_x_t(const XArgs& a, cudaStream_t st) {
+static cudaError_t launch_x_t(const XArgs& a_in, cudaStream_t st) {
+  XArgs a = a_in;
   const int threads = a.spc << a.log2tsys;
   if (threads % 32 != 0 || threads > MAXT) return cudaErrorInvalidValue;  // whole warps only
   int blocks = (a.ny + a.spc - 1) / a.spc;
-  const size_t sm = x_smem_bytes(a.spc, 1 << a.log2tsys, sizeof(T) == 8, TREE);
+  size_t sm = x_smem_bytes(a.spc, 1 << a.log2tsys, sizeof(T) == 8, TREE);
+  a.stage_off = -1;
+  if (sizeof(T) == 4 && a.stage_mode == 1) {  // staging area after the solver's region
+    a.stage_off = (int)align64(sm);
+    sm = align64(sm) + x_stage_bytes(threads, K);
+    if (sm > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
+  }
   if (a.persist) {  // one wave of resident CTAs
     int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
@@ -220,6 +554,108 @@ static cudaError_t launch_y_t(const YArgs& a_in, cudaStream_t st) {
 
 // K = 4, 8 fit 64 registers; K = 16, 32 take the smallest bound that holds
 // `threads` (float only; FP64 kernels are bounded at 512).
+template <int K, int MAXT>
+static cudaError_t launch_x_pipe_t(const XArgs& a_in, const CUtensorMap& tu, const CUtensorMap& tm,
+                                   cudaStream_t st) {
+  XArgs a = a_in;
+  const int tsys = 1 << a.log2tsys;
+  const int threads = a.spc * tsys;
+  if (threads % 32 != 0 || threads > MAXT || tsys * K < 256) return cudaErrorInvalidValue;
+  a.stage_off = (int)align64(x_smem_bytes(a.spc, tsys, false, true));
+  const size_t sm = x_pipe_smem_bytes(a.spc, tsys, K);
+  if (sm > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
+  const int nblk = (a.ny + a.spc - 1) / a.spc;
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, x_pipe_kernel<K, MAXT>, threads, sm);
+  if (e != cudaSuccess) return e;
+  const int blocks = std::max(1, std::min(nblk, nsm * std::max(per_sm, 1)));
+  x_pipe_kernel<K, MAXT><<<blocks, threads, sm, st>>>(a, tu, tm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_x_pipe(const XArgs& a, int K, const CUtensorMap& tu, const CUtensorMap& tm,
+                          cudaStream_t st) {
+  const int threads = a.spc << a.log2tsys;
+  switch (K) {
+    case 8: return launch_x_pipe_t<8, 1024>(a, tu, tm, st);
+    case 16:
+      if (threads <= 256) return launch_x_pipe_t<16, 256>(a, tu, tm, st);
+      if (threads <= 512) return launch_x_pipe_t<16, 512>(a, tu, tm, st);
+      return launch_x_pipe_t<16, 1024>(a, tu, tm, st);
+    case 32:
+      if (threads <= 256) return launch_x_pipe_t<32, 256>(a, tu, tm, st);
+      return launch_x_pipe_t<32, 512>(a, tu, tm, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+size_t y_pipe_smem_bytes(int C, int tcol, int K) {
+  const size_t R = (size_t)tcol * K;
+  return align64(y_smem_bytes(16, C, tcol, false, true)) + 8 + 128 + 2 * R * 16 * 4;
+}
+
+int y_pipe_box_rows(int tcol, int K) {
+  const int R = tcol * K;
+  return R < 256 ? R : 256;
+}
+
+// Tensor map of a pitched [ny][ld] FP32 field as 2D {ld, ny}, boxes of
+// {16, box_rows}, no swizzle, zero fill outside.
+cudaError_t encode_strip_map(CUtensorMap* out, const float* base, int ld, int ny, int box_rows) {
+  EncodeTiledFn fn = nullptr;
+  cudaError_t e = get_encode_fn(&fn);
+  if (e != cudaSuccess) return e;
+  if (ld % 32 != 0 || box_rows < 1 || box_rows > 256 || ((uintptr_t)base & 15) != 0)
+    return cudaErrorInvalidValue;
+  const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)ny};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  const cuuint32_t box[2] = {16, (cuuint32_t)box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  const CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims,
+                        strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int K, int MAXT>
+static cudaError_t launch_y_pipe_t(const YArgs& a_in, const YMaps& mp, cudaStream_t st) {
+  YArgs a = a_in;
+  const int tcol = 1 << a.log2tcol;
+  const int threads = 16 * tcol;
+  if (a.log2W != 4 || threads % 32 != 0 || threads > MAXT || tcol * K < 64) return cudaErrorInvalidValue;
+  a.stage_off = (int)align64(y_smem_bytes(16, a.C, tcol, false, true));
+  const size_t sm = y_pipe_smem_bytes(a.C, tcol, K);
+  if (sm > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
+  const int strips = (a.nx + 15) / 16;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(strips * a.C, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = a.C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nc = 0;
+  cudaError_t e = cudaOccupancyMaxActiveClusters(&nc, y_pipe_kernel<K, MAXT>, &cfg);
+  if (e != cudaSuccess) return e;
+  cfg.gridDim = dim3(std::max(1, std::min(strips, nc)) * a.C, 1, 1);
+  return cudaLaunchKernelEx(&cfg, y_pipe_kernel<K, MAXT>, a, mp.w, mp.m, mp.uc, mp.up);
+}
+
+cudaError_t launch_y_pipe(const YArgs& a, int K, const YMaps& mp, cudaStream_t st) {
+  const int threads = 1 << (a.log2W + a.log2tcol);
+  if (K == 16) return threads <= 256 ? launch_y_pipe_t<16, 256>(a, mp, st) : launch_y_pipe_t<16, 512>(a, mp, st);
+  if (K == 32) return threads <= 256 ? launch_y_pipe_t<32, 256>(a, mp, st) : launch_y_pipe_t<32, 512>(a, mp, st);
+  return cudaErrorInvalidValue;
+}
+
 #define ADI_DISPATCH_K(FN, TT, MT, TR, ARGS)             \
   switch (K) {                                           \
     case 4: return FN<4, TT, MT, TR> ARGS;               \
@@ -301,6 +737,16 @@ cudaError_t configure_kernels() {
   ADI_CFG_SMALL(x_sweep_kernel, false, false)
   ADI_CFG_SMALL(y_sweep_kernel, true, true)
   ADI_CFG_SMALL(y_sweep_kernel, false, true)
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<16, 256>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<16, 512>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<32, 256>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<32, 512>, true);
+  if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<8, 1024>, false);
+  if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<16, 256>, false);
+  if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<16, 512>, false);
+  if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<16, 1024>, false);
+  if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<32, 256>, false);
+  if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<32, 512>, false);
   return e;
 }
 

@@ -1,6 +1,7 @@
 // adi_internal.h -- host/device structures shared by the library's .cu files.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -37,6 +38,9 @@ struct XArgs {
   double src_scale; // tau^2 / (h1 h2)
   const GridDev* gd;
   int persist;      // 1: persistent CTAs loop over row blocks (grid set by the launcher)
+  int stage_mode;   // 1: rows staged through shared memory (FP32), 2: direct loads, 3: TMA pipeline
+  int stage_off;    // byte offset of the staging area (set by the launcher), -1: none
+  int* err;         // device error word (bounded waits), or null
 };
 
 // Arguments of the y-sweep + update kernel (Eq. fr2's y operator).
@@ -72,6 +76,21 @@ cudaError_t launch_scan_m(const float* m, int nx, int ny, int ld, unsigned int* 
 size_t x_smem_bytes(int spc, int tsys, bool fp64, bool tree);
 size_t y_smem_bytes(int W, int C, int tcol, bool fp64, bool tree);
 size_t y_stage_bytes(int threads, int K);
+size_t x_stage_bytes(int threads, int K);
+size_t x_pipe_smem_bytes(int spc, int tsys, int K);
+int x_pipe_box_lines(int tsys, int K);
+size_t y_pipe_smem_bytes(int C, int tcol, int K);
+int y_pipe_box_rows(int tcol, int K);
+cudaError_t encode_strip_map(CUtensorMap* out, const float* base, int ld, int ny, int box_rows);
+// Strip maps of the pipelined y sweep: w, m, u^k, u^{k-1}.
+struct YMaps {
+  CUtensorMap w, m, uc, up;
+};
+cudaError_t launch_y_pipe(const YArgs& a, int K, const YMaps& mp, cudaStream_t st);
+// Row tensor map for the pipelined x sweep (see adi_tma.cuh).
+cudaError_t encode_row_map(CUtensorMap* out, const float* base, int ld, int ny, int box_lines);
+cudaError_t launch_x_pipe(const XArgs& a, int K, const CUtensorMap& tu, const CUtensorMap& tm,
+                          cudaStream_t st);
 constexpr int kMaxDynSmem = 227 * 1024;
 cudaError_t configure_kernels();
 

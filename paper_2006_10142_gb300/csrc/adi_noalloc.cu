@@ -115,7 +115,7 @@ extern "C" int adi_wave_step_noalloc(const adi_wave_desc* desc, int32_t ld, doub
   G.hy = d.ly / (d.ny + 1);
   G.fp64mode = d.fp64_solve;
   G.mmax = m_max;
-  const adi_wave_tuning t = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const adi_wave_tuning t = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   std::string why;
   rc = plan_grid(G, t, why);
   if (rc != ADI_OK) return fail_msg(rc, why);
@@ -149,6 +149,9 @@ extern "C" int adi_wave_step_noalloc(const adi_wave_desc* desc, int32_t ld, doub
   xa.src_scale = d.dt * d.dt / (G.hx * G.hy);
   xa.gd = slot->gd;
   xa.persist = 0;
+  xa.stage_mode = P.x_stage;
+  xa.stage_off = -1;
+  xa.err = nullptr;
   YArgs ya;
   ya.nx = d.nx;
   ya.ny = d.ny;
@@ -168,9 +171,29 @@ extern "C" int adi_wave_step_noalloc(const adi_wave_desc* desc, int32_t ld, doub
   ya.sc = d.dt * d.dt / (2.0 * G.hy * G.hy);
   ya.gd = slot->gd;
   ya.err = nullptr;
-  e = launch_x(xa, P.kx, P.fp64x, P.tree, st);
+  if (P.x_stage == 3) {  // host-side tensor maps of the caller's buffers (no allocation)
+    const int L = x_pipe_box_lines(1 << P.log2tsys, P.kx);
+    CUtensorMap tu, tm;
+    e = encode_row_map(&tu, u_cur, ld, d.ny, L);
+    if (e == cudaSuccess) e = encode_row_map(&tm, m, ld, d.ny, L);
+    if (e != cudaSuccess) return fail_msg(ADI_ECUDA, std::string("tensor maps: ") + cudaGetErrorString(e));
+    e = launch_x_pipe(xa, P.kx, tu, tm, st);
+  } else {
+    e = launch_x(xa, P.kx, P.fp64x, P.tree, st);
+  }
   if (e != cudaSuccess) return fail_msg(ADI_ECUDA, std::string("x sweep launch: ") + cudaGetErrorString(e));
-  e = launch_y(ya, P.ky, P.fp64y, P.tree, st);
+  if (P.y_stage == 3) {
+    const int BH = y_pipe_box_rows(1 << P.log2tcol, P.ky);
+    YMaps mp;
+    e = encode_strip_map(&mp.w, slot->w, ld, d.ny, BH);
+    if (e == cudaSuccess) e = encode_strip_map(&mp.m, m, ld, d.ny, BH);
+    if (e == cudaSuccess) e = encode_strip_map(&mp.uc, u_cur, ld, d.ny, BH);
+    if (e == cudaSuccess) e = encode_strip_map(&mp.up, u_prev, ld, d.ny, BH);
+    if (e != cudaSuccess) return fail_msg(ADI_ECUDA, std::string("strip maps: ") + cudaGetErrorString(e));
+    e = launch_y_pipe(ya, P.ky, mp, st);
+  } else {
+    e = launch_y(ya, P.ky, P.fp64y, P.tree, st);
+  }
   if (e != cudaSuccess) return fail_msg(ADI_ECUDA, std::string("y sweep launch: ") + cudaGetErrorString(e));
   return ADI_OK;
 }

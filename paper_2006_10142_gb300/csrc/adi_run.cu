@@ -277,6 +277,9 @@ int adi_wave::launch_fwd(Grid& G, const float* u_cur, float* u_prev, float* w, f
   xa.src_scale = G.dt * G.dt / (G.hx * G.hy);
   xa.gd = gd;
   xa.persist = P.persist;
+  xa.stage_mode = P.x_stage;
+  xa.stage_off = -1;
+  xa.err = d_err;
   YArgs ya;
   ya.nx = G.nx;
   ya.ny = G.ny;
@@ -299,10 +302,50 @@ int adi_wave::launch_fwd(Grid& G, const float* u_cur, float* u_prev, float* w, f
 
   cudaEvent_t a = nullptr;
   if (profile && prof_begin(st, &a) != ADI_OK) return ADI_ECUDA;
-  CK(launch_x(xa, P.kx, P.fp64x, P.tree, st), "x sweep launch");
+  if (P.x_stage == 3) {
+    const int L = x_pipe_box_lines(1 << P.log2tsys, P.kx);
+    if (G.tm_lines != L) {
+      CK(encode_row_map(&G.tm_buf[0], G.buf[0], G.ld, G.ny, L), "tensor map u0");
+      CK(encode_row_map(&G.tm_buf[1], G.buf[1], G.ld, G.ny, L), "tensor map u1");
+      CK(encode_row_map(&G.tm_m, G.m, G.ld, G.ny, L), "tensor map m");
+      G.tm_lines = L;
+    }
+    CUtensorMap tmp;
+    const CUtensorMap* tu = u_cur == G.buf[0] ? &G.tm_buf[0] : u_cur == G.buf[1] ? &G.tm_buf[1] : nullptr;
+    if (tu == nullptr) {
+      CK(encode_row_map(&tmp, u_cur, G.ld, G.ny, L), "tensor map u");
+      tu = &tmp;
+    }
+    CK(launch_x_pipe(xa, P.kx, *tu, G.tm_m, st), "x sweep launch");
+  } else {
+    CK(launch_x(xa, P.kx, P.fp64x, P.tree, st), "x sweep launch");
+  }
   if (profile && prof_end(st, a, ADI_KERNEL_X) != ADI_OK) return ADI_ECUDA;
   if (profile && prof_begin(st, &a) != ADI_OK) return ADI_ECUDA;
-  CK(launch_y(ya, P.ky, P.fp64y, P.tree, st), "y sweep launch");
+  if (P.y_stage == 3) {
+    const int BH = y_pipe_box_rows(1 << P.log2tcol, P.ky);
+    if (G.ts_rows != BH) {
+      CK(encode_strip_map(&G.ts_buf[0], G.buf[0], G.ld, G.ny, BH), "strip map u0");
+      CK(encode_strip_map(&G.ts_buf[1], G.buf[1], G.ld, G.ny, BH), "strip map u1");
+      CK(encode_strip_map(&G.ts_m, G.m, G.ld, G.ny, BH), "strip map m");
+      CK(encode_strip_map(&G.ts_w, G.w, G.ld, G.ny, BH), "strip map w");
+      G.ts_rows = BH;
+    }
+    YMaps mp;
+    mp.m = G.ts_m;
+    const float* want[3] = {w, u_cur, u_prev};
+    CUtensorMap* outm[3] = {&mp.w, &mp.uc, &mp.up};
+    for (int f = 0; f < 3; ++f) {
+      const float* p = want[f];
+      if (p == G.w) *outm[f] = G.ts_w;
+      else if (p == G.buf[0]) *outm[f] = G.ts_buf[0];
+      else if (p == G.buf[1]) *outm[f] = G.ts_buf[1];
+      else CK(encode_strip_map(outm[f], p, G.ld, G.ny, BH), "strip map");
+    }
+    CK(launch_y_pipe(ya, P.ky, mp, st), "y sweep launch");
+  } else {
+    CK(launch_y(ya, P.ky, P.fp64y, P.tree, st), "y sweep launch");
+  }
   if (profile && prof_end(st, a, ADI_KERNEL_Y) != ADI_OK) return ADI_ECUDA;
   launches += 2;
   return ADI_OK;

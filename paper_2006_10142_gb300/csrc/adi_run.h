@@ -28,6 +28,7 @@ struct GridPlan {
   int cta_threads = 0, cta_threads_y = 0;
   int y_stage = 1;   // 1: shared-memory staging, 2: L2 prefetch
   int persist = 0;   // 1: persistent sweeps with L2 prefetch of the next tile
+  int x_stage = 2;   // 1: rows staged through shared memory, 2: direct, 3: TMA pipeline
 };
 
 struct Grid {
@@ -44,6 +45,10 @@ struct Grid {
   GridDev hgd = {};                 // host mirror
   double mmin = 0, mmax = 0;
   GridPlan plan;
+  CUtensorMap tm_buf[2], tm_m;      // row maps of buf[0], buf[1], m (pipelined x sweep)
+  int tm_lines = 0;                 // box height they were encoded with, 0 = none
+  CUtensorMap ts_buf[2], ts_m, ts_w;  // strip maps (pipelined y sweep)
+  int ts_rows = 0;                  // box rows they were encoded with, 0 = none
 };
 
 // What adi_wave_adjoint needs to replay the last run.
@@ -90,7 +95,7 @@ struct adi_wave {
   int rec_cap = 0;
   cudaStream_t cap = nullptr;  // private stream used only for graph capture
   cudaGraphExec_t pair[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [orientation][gather]
-  adi_wave_tuning tuning = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  adi_wave_tuning tuning = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   int ckpt_every = 0;
   adi::RunRecord rr;
   adi::AdjWork aw;

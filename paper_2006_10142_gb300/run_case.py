@@ -20,7 +20,7 @@ import math
 import numpy as np
 
 TUNING_KEYS = ("chunk_x", "chunk_y", "rows_per_cta", "cols_per_cta", "pcr_size", "use_graph",
-               "solver", "cta_threads", "cta_threads_y", "y_stage", "persist")
+               "solver", "cta_threads", "cta_threads_y", "y_stage", "persist", "x_stage")
 
 
 def main(argv=None):
