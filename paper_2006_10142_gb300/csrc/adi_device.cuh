@@ -381,4 +381,45 @@ __device__ __forceinline__ void pcr64(Eq<T>& E0, Eq<T>& E1, int lane, int n_eq) 
   }
 }
 
+// Partition step in two independent halves (K >= 32): each half is
+// reduced to its two interface equations (two short elimination chains the
+// compiler can interleave) and the halves are merged into the chunk's
+// summary; `nd` keeps the merge for chunk_backsub_split.  Below K = 32 this
+// is chunk_reduce itself.
+template <int K, typename T>
+__device__ __forceinline__ void chunk_reduce_split(T (&d)[K], T (&s)[K], Seg<T>& S, Node<T>& nd) {
+  if constexpr (K >= 32) {
+    constexpr int H = K / 2;
+    T(&dA)[H] = *reinterpret_cast<T(*)[H]>(&d[0]);
+    T(&sA)[H] = *reinterpret_cast<T(*)[H]>(&s[0]);
+    T(&dB)[H] = *reinterpret_cast<T(*)[H]>(&d[H]);
+    T(&sB)[H] = *reinterpret_cast<T(*)[H]>(&s[H]);
+    Seg<T> A, B;
+    chunk_reduce<H, T>(dA, sA, A.f, A.l);
+    chunk_reduce<H, T>(dB, sB, B.f, B.l);
+    S = seg_merge(A, B, nd);
+  } else {
+    chunk_reduce<K, T>(d, s, S.f, S.l);
+  }
+}
+
+// Back substitution matching chunk_reduce_split: x_0 = xa, x_{K-1} = xc.
+template <int K, typename T>
+__device__ __forceinline__ void chunk_backsub_split(T (&d)[K], const T (&s)[K], const Node<T>& nd,
+                                                    T xa, T xc) {
+  if constexpr (K >= 32) {
+    constexpr int H = K / 2;
+    T(&dA)[H] = *reinterpret_cast<T(*)[H]>(&d[0]);
+    const T(&sA)[H] = *reinterpret_cast<const T(*)[H]>(&s[0]);
+    T(&dB)[H] = *reinterpret_cast<T(*)[H]>(&d[H]);
+    const T(&sB)[H] = *reinterpret_cast<const T(*)[H]>(&s[H]);
+    const T xb = fma(nd.xbc, xc, fma(nd.xba, xa, nd.xb0));  // x_{H-1}
+    const T xb1 = fma(nd.ybc, xc, fma(nd.yba, xa, nd.y0));  // x_H
+    chunk_backsub<H, T>(dA, sA, xa, xb);
+    chunk_backsub<H, T>(dB, sB, xb1, xc);
+  } else {
+    chunk_backsub<K, T>(d, s, xa, xc);
+  }
+}
+
 }  // namespace adi

@@ -91,9 +91,11 @@ __device__ __forceinline__ float stage_at(const float* row, int e) {
 template <int K, int MAXT>
 __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
     x_pipe_kernel(const XArgs a, const __grid_constant__ CUtensorMap tm_u,
-                  const __grid_constant__ CUtensorMap tm_m) {
+                  const __grid_constant__ CUtensorMap tm_m, const __grid_constant__ CUtensorMap tm_w) {
   extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int NQ = K / 4;
   const int tid = threadIdx.x;
+  const int lane = tid & 31;
   const int tsys = 1 << a.log2tsys;
   const int rowf = tsys * K;               // floats per staged row (a power of two >= 256)
   const int lines = rowf >> 5;             // 128-byte lines per staged row
@@ -103,8 +105,10 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
   const uint32_t bar = sa + (uint32_t)a.stage_off;
   const uint32_t st_u = (bar + 8u + 1023u) & ~1023u;
   const uint32_t st_m = st_u + (uint32_t)(a.spc * rowf * 4);
+  const uint32_t st_w = st_m + (uint32_t)(a.spc * rowf * 4);
   const float* su = reinterpret_cast<const float*>(smem + (st_u - sa));
   const float* sm = su + (size_t)a.spc * rowf;
+  float4* sw4 = reinterpret_cast<float4*>(smem + (st_w - sa));
   const int nblk = (a.ny + a.spc - 1) / a.spc;
   const uint32_t pf_bytes = (uint32_t)((a.nx * 4 + 15) & ~15);
 
@@ -113,19 +117,20 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
     mbar_fence_init();
   }
   __syncthreads();
-  // thread 0: announce and start the copies of block `blk`
+  // warp 0: announce and start the copies of block `blk` (one box per lane)
   auto issue = [&](int blk) {
     const int j0 = blk * a.spc;
     const int nrows = min(a.spc, a.ny - j0);
-    mbar_arrive_expect_tx(bar, (uint32_t)(2 * nrows * rowf * 4));
-    for (int r = 0; r < nrows; ++r)
-      for (int c = 0; c < nchunk; ++c) {
-        const uint32_t off = (uint32_t)((r * rowf + c * L * 32) * 4);
-        tma_load_3d(st_u + off, &tm_u, 0, c * L, j0 + r, bar);
-        tma_load_3d(st_m + off, &tm_m, 0, c * L, j0 + r, bar);
-      }
+    if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(2 * nrows * rowf * 4));
+    for (int t = lane; t < 2 * nrows * nchunk; t += 32) {
+      const int f = t & 1, rc = t >> 1;
+      const int r = rc / nchunk, c = rc - r * nchunk;
+      const uint32_t off = (uint32_t)((r * rowf + c * L * 32) * 4);
+      if (f == 0) tma_load_3d(st_u + off, &tm_u, 0, c * L, j0 + r, bar);
+      else tma_load_3d(st_m + off, &tm_m, 0, c * L, j0 + r, bar);
+    }
   };
-  if (tid == 0 && (int)blockIdx.x < nblk) issue(blockIdx.x);
+  if (tid < 32 && (int)blockIdx.x < nblk) issue(blockIdx.x);
 
   const int sys = tid >> a.log2tsys;
   const int p = tid & (tsys - 1);
@@ -186,18 +191,36 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
 #pragma unroll
       for (int k = 0; k < K; ++k) { d[k] = 0.f; s[k] = 0.f; }
     }
+    if (tid < 32) bulk_wait_read();  // the previous block's w stage has been read out (per-lane groups)
     __syncthreads();  // every read of the stage is done: it may be refilled
     const int next = blk + (int)gridDim.x;
-    if (tid == 0 && next < nblk) {
+    if (tid < 32 && next < nblk) {
       fence_proxy_async_smem();
       issue(next);
-      const int jl = next * a.spc - 1, jh = next * a.spc + a.spc;
-      if (jl >= 0) l2_prefetch_bulk(a.u + (size_t)jl * a.ld, pf_bytes);
-      if (jh < a.ny) l2_prefetch_bulk(a.u + (size_t)jh * a.ld, pf_bytes);
+      if (lane == 0) {
+        const int jl = next * a.spc - 1, jh = next * a.spc + a.spc;
+        if (jl >= 0) l2_prefetch_bulk(a.u + (size_t)jl * a.ld, pf_bytes);
+        if (jh < a.ny) l2_prefetch_bulk(a.u + (size_t)jh * a.ld, pf_bytes);
+      }
     }
     x_solve_rows<K, float, true>(smem, a.spc, a.log2tsys, a.pcr, sys, p, d, s);
-    if (active) store_vec<K, float>(a.w + (size_t)j * a.ld + i0, d);
+    // w through the swizzled stage, stored by TMA boxes
+#pragma unroll
+    for (int c = 0; c < NQ; ++c)
+      sw4[swz4((sys * rowf + i0) / 4 + c)] = make_float4(d[4 * c + 0], d[4 * c + 1], d[4 * c + 2], d[4 * c + 3]);
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid < 32) {
+      const int j0 = blk * a.spc;
+      const int nrows = min(a.spc, a.ny - j0);
+      for (int t = lane; t < nrows * nchunk; t += 32) {
+        const int r = t / nchunk, c = t - r * nchunk;
+        tma_store_3d(&tm_w, 0, c * L, j0 + r, st_w + (uint32_t)((r * rowf + c * L * 32) * 4));
+      }
+      bulk_commit();
+    }
   }
+  if (tid < 32) bulk_wait_all();
   if (timed_out && (tid & 31) == 0 && a.err) atomicOr(a.err, ERR_TIMEOUT);
 }
 
@@ -270,19 +293,22 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
     mbar_fence_init();
   }
   __syncthreads();
-  // thread 0: copies of strip `st` (this CTA's rows) and L2 prefetch of its u boxes
+  // warp 0: copies of strip `st` (this CTA's rows) and L2 prefetch of its
+  // u boxes, one box per lane
+  const int lane = tid & 31;
   auto issue = [&](int st) {
-    mbar_arrive_expect_tx(bar, (uint32_t)(2 * R * W * 4));
-    for (int b = 0; b < nbox; ++b) {
+    if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(2 * R * W * 4));
+    for (int t = lane; t < 4 * nbox; t += 32) {
+      const int b = t >> 2, f = t & 3;
       const uint32_t off = (uint32_t)(b * BH * W * 4);
-      tma_load_2d(st_w + off, &tm_w, st * W, row0 + b * BH, bar);
-      tma_load_2d(st_m + off, &tm_m, st * W, row0 + b * BH, bar);
-      tma_prefetch_2d(&tm_uc, st * W, row0 + b * BH);
-      tma_prefetch_2d(&tm_up, st * W, row0 + b * BH);
+      if (f == 0) tma_load_2d(st_w + off, &tm_w, st * W, row0 + b * BH, bar);
+      else if (f == 1) tma_load_2d(st_m + off, &tm_m, st * W, row0 + b * BH, bar);
+      else if (f == 2) tma_prefetch_2d(&tm_uc, st * W, row0 + b * BH);
+      else tma_prefetch_2d(&tm_up, st * W, row0 + b * BH);
     }
   };
   int strip = blockIdx.x / C;
-  if (tid == 0 && strip < nstrips) issue(strip);
+  if (tid < 32 && strip < nstrips) issue(strip);
   const int col = tid & (W - 1);
   const int q = tid >> 4;
   const int gq = rank * tcol + q;
@@ -306,26 +332,29 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
     }
     __syncthreads();  // the stage is consumed: refill it with the next strip
     const int next = strip + ncl;
-    if (tid == 0 && next < nstrips) {
+    if (tid < 32 && next < nstrips) {
       fence_proxy_async_smem();
       issue(next);
     }
-    y_solve_cols<K, float, true>(smem, a.log2W, a.log2tcol, C, rank, a.pcr, col, gq, d, s);
+    // the cluster barrier at the top of the next strip keeps the owners'
+    // shared memory alive until every remote read is done
+    y_solve_cols<K, float, true>(smem, a.log2W, a.log2tcol, C, rank, a.pcr, col, gq, d, s, false);
     if (colok) {
       const size_t base = (size_t)j0 * ld + i;
       float chk = 0.f;
       if (j0 + K <= a.ny) {
-        // groups of 8 rows: 16 loads in flight per thread within the register budget
+        // groups of EG rows: 2 EG loads in flight per thread within the register budget
+        constexpr int EG = K < 16 ? K : 16;
 #pragma unroll
-        for (int g = 0; g < K; g += 8) {
-          float uc[8], up[8];
+        for (int g = 0; g < K; g += EG) {
+          float uc[EG], up[EG];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {
+          for (int k = 0; k < EG; ++k) {
             uc[k] = __ldcg(a.u_cur + base + (g + k) * ld);
             up[k] = __ldcg(a.u_prev + base + (g + k) * ld);
           }
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {
+          for (int k = 0; k < EG; ++k) {
             const float un = 2.0f * uc[k] - up[k] + d[g + k];
             a.u_prev[base + (g + k) * ld] = un;
             chk += un - un;
@@ -351,6 +380,7 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
     if (strip == 0 && rank == 0 && tid == 0 && a.gd) a.gd->k += 1;
     __syncthreads();  // the solver's shared memory is reused by the next strip
   }
+  if (C > 1) cgx::this_cluster().sync();  // no CTA leaves while its shared memory may be read
   if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0 && a.err) atomicOr(a.err, ERR_NUMERIC);
   if (timed_out && (tid & 31) == 0 && a.err) atomicOr(a.err, ERR_TIMEOUT);
 }
@@ -451,7 +481,7 @@ size_t y_smem_bytes(int W, int C, int tcol, bool fp64, bool tree) {
 size_t y_stage_bytes(int threads, int K) { return align64((size_t)2 * K * threads * sizeof(float)); }
 size_t x_stage_bytes(int threads, int K) { return align64((size_t)2 * K * threads * sizeof(float)); }
 size_t x_pipe_smem_bytes(int spc, int tsys, int K) {
-  return align64(x_smem_bytes(spc, tsys, false, true)) + 8 + 1024 + (size_t)2 * spc * tsys * K * 4;
+  return align64(x_smem_bytes(spc, tsys, false, true)) + 8 + 1024 + (size_t)3 * spc * tsys * K * 4;
 }
 
 // Tensor map of a pitched [ny][ld] FP32 field as {32, ld/32, ny} with
@@ -556,7 +586,7 @@ static cudaError_t launch_y_t(const YArgs& a_in, cudaStream_t st) {
 // `threads` (float only; FP64 kernels are bounded at 512).
 template <int K, int MAXT>
 static cudaError_t launch_x_pipe_t(const XArgs& a_in, const CUtensorMap& tu, const CUtensorMap& tm,
-                                   cudaStream_t st) {
+                                   const CUtensorMap& tw, cudaStream_t st) {
   XArgs a = a_in;
   const int tsys = 1 << a.log2tsys;
   const int threads = a.spc * tsys;
@@ -572,22 +602,22 @@ static cudaError_t launch_x_pipe_t(const XArgs& a_in, const CUtensorMap& tu, con
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, x_pipe_kernel<K, MAXT>, threads, sm);
   if (e != cudaSuccess) return e;
   const int blocks = std::max(1, std::min(nblk, nsm * std::max(per_sm, 1)));
-  x_pipe_kernel<K, MAXT><<<blocks, threads, sm, st>>>(a, tu, tm);
+  x_pipe_kernel<K, MAXT><<<blocks, threads, sm, st>>>(a, tu, tm, tw);
   return cudaGetLastError();
 }
 
 cudaError_t launch_x_pipe(const XArgs& a, int K, const CUtensorMap& tu, const CUtensorMap& tm,
-                          cudaStream_t st) {
+                          const CUtensorMap& tw, cudaStream_t st) {
   const int threads = a.spc << a.log2tsys;
   switch (K) {
-    case 8: return launch_x_pipe_t<8, 1024>(a, tu, tm, st);
+    case 8: return launch_x_pipe_t<8, 1024>(a, tu, tm, tw, st);
     case 16:
-      if (threads <= 256) return launch_x_pipe_t<16, 256>(a, tu, tm, st);
-      if (threads <= 512) return launch_x_pipe_t<16, 512>(a, tu, tm, st);
-      return launch_x_pipe_t<16, 1024>(a, tu, tm, st);
+      if (threads <= 256) return launch_x_pipe_t<16, 256>(a, tu, tm, tw, st);
+      if (threads <= 512) return launch_x_pipe_t<16, 512>(a, tu, tm, tw, st);
+      return launch_x_pipe_t<16, 1024>(a, tu, tm, tw, st);
     case 32:
-      if (threads <= 256) return launch_x_pipe_t<32, 256>(a, tu, tm, st);
-      return launch_x_pipe_t<32, 512>(a, tu, tm, st);
+      if (threads <= 256) return launch_x_pipe_t<32, 256>(a, tu, tm, tw, st);
+      return launch_x_pipe_t<32, 512>(a, tu, tm, tw, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -90,7 +90,7 @@ cudaError_t launch_y_pipe(const YArgs& a, int K, const YMaps& mp, cudaStream_t s
 // Row tensor map for the pipelined x sweep (see adi_tma.cuh).
 cudaError_t encode_row_map(CUtensorMap* out, const float* base, int ld, int ny, int box_lines);
 cudaError_t launch_x_pipe(const XArgs& a, int K, const CUtensorMap& tu, const CUtensorMap& tm,
-                          cudaStream_t st);
+                          const CUtensorMap& tw, cudaStream_t st);
 constexpr int kMaxDynSmem = 227 * 1024;
 cudaError_t configure_kernels();
 

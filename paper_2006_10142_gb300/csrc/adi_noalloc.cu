@@ -173,11 +173,12 @@ extern "C" int adi_wave_step_noalloc(const adi_wave_desc* desc, int32_t ld, doub
   ya.err = nullptr;
   if (P.x_stage == 3) {  // host-side tensor maps of the caller's buffers (no allocation)
     const int L = x_pipe_box_lines(1 << P.log2tsys, P.kx);
-    CUtensorMap tu, tm;
+    CUtensorMap tu, tm, tw;
     e = encode_row_map(&tu, u_cur, ld, d.ny, L);
     if (e == cudaSuccess) e = encode_row_map(&tm, m, ld, d.ny, L);
+    if (e == cudaSuccess) e = encode_row_map(&tw, slot->w, ld, d.ny, L);
     if (e != cudaSuccess) return fail_msg(ADI_ECUDA, std::string("tensor maps: ") + cudaGetErrorString(e));
-    e = launch_x_pipe(xa, P.kx, tu, tm, st);
+    e = launch_x_pipe(xa, P.kx, tu, tm, tw, st);
   } else {
     e = launch_x(xa, P.kx, P.fp64x, P.tree, st);
   }

@@ -308,15 +308,21 @@ int adi_wave::launch_fwd(Grid& G, const float* u_cur, float* u_prev, float* w, f
       CK(encode_row_map(&G.tm_buf[0], G.buf[0], G.ld, G.ny, L), "tensor map u0");
       CK(encode_row_map(&G.tm_buf[1], G.buf[1], G.ld, G.ny, L), "tensor map u1");
       CK(encode_row_map(&G.tm_m, G.m, G.ld, G.ny, L), "tensor map m");
+      CK(encode_row_map(&G.tm_w, G.w, G.ld, G.ny, L), "tensor map w");
       G.tm_lines = L;
     }
-    CUtensorMap tmp;
+    CUtensorMap tmp, tmpw;
     const CUtensorMap* tu = u_cur == G.buf[0] ? &G.tm_buf[0] : u_cur == G.buf[1] ? &G.tm_buf[1] : nullptr;
     if (tu == nullptr) {
       CK(encode_row_map(&tmp, u_cur, G.ld, G.ny, L), "tensor map u");
       tu = &tmp;
     }
-    CK(launch_x_pipe(xa, P.kx, *tu, G.tm_m, st), "x sweep launch");
+    const CUtensorMap* tw = &G.tm_w;
+    if (w != G.w) {
+      CK(encode_row_map(&tmpw, w, G.ld, G.ny, L), "tensor map w");
+      tw = &tmpw;
+    }
+    CK(launch_x_pipe(xa, P.kx, *tu, G.tm_m, *tw, st), "x sweep launch");
   } else {
     CK(launch_x(xa, P.kx, P.fp64x, P.tree, st), "x sweep launch");
   }

@@ -45,7 +45,7 @@ struct Grid {
   GridDev hgd = {};                 // host mirror
   double mmin = 0, mmax = 0;
   GridPlan plan;
-  CUtensorMap tm_buf[2], tm_m;      // row maps of buf[0], buf[1], m (pipelined x sweep)
+  CUtensorMap tm_buf[2], tm_m, tm_w;  // row maps of buf[0], buf[1], m, w (pipelined x sweep)
   int tm_lines = 0;                 // box height they were encoded with, 0 = none
   CUtensorMap ts_buf[2], ts_m, ts_w;  // strip maps (pipelined y sweep)
   int ts_rows = 0;                  // box rows they were encoded with, 0 = none

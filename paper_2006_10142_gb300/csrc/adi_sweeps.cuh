@@ -98,7 +98,8 @@ __device__ __forceinline__ void x_solve_rows(unsigned char* smem, int spc, int l
     const int levels = log2tsys < 5 ? log2tsys : 5;
     Node<T>* nodes = reinterpret_cast<Node<T>*>(smem) + warp * 31;
     Seg<T> S;
-    chunk_reduce<K, T>(d, s, S.f, S.l);
+    Node<T> ndc;
+    chunk_reduce_split<K, T>(d, s, S, ndc);
     S = warp_tree_up<T>(S, nodes, lane, levels);
     T xa, xc;
     if (log2tsys <= 5) {
@@ -127,7 +128,7 @@ __device__ __forceinline__ void x_solve_rows(unsigned char* smem, int spc, int l
       xc = xtop[2 * (sys * nw + wis) + 1];
     }
     warp_tree_down<T>(nodes, lane, levels, xa, xc);
-    chunk_backsub<K, T>(d, s, xa, xc);
+    chunk_backsub_split<K, T>(d, s, ndc, xa, xc);
   } else {
     const int N = 2 << log2tsys;
     Eq<T>* red = reinterpret_cast<Eq<T>*>(smem);
@@ -168,10 +169,15 @@ __device__ __forceinline__ int cluster_rank(int C) {
 // cluster rank (col mod C), reached over DSMEM.  All threads of every CTA of
 // the cluster must call this; with C > 1 the caller has executed
 // cluster_arrive_early() at kernel start.
+// final_sync = false (tree solver only) leaves out the last cluster barrier,
+// which only keeps the owners' shared memory alive until every remote read
+// is done; a persistent caller may drop it because its next cluster barrier
+// comes after those reads, and it must then synchronise the cluster once
+// before exit.
 template <int K, typename T, bool TREE>
 __device__ __forceinline__ void y_solve_cols(unsigned char* smem, int log2W, int log2tcol, int C,
                                              int rank, int pcr, int col, int gq, T (&d)[K],
-                                             T (&s)[K]) {
+                                             T (&s)[K], bool final_sync = true) {
   const int W = 1 << log2W;
   // C, W, tcol and the group counts are powers of two: shifts, not divisions
   const int log2C = 31 - __clz(C);
@@ -194,9 +200,10 @@ __device__ __forceinline__ void y_solve_cols(unsigned char* smem, int log2W, int
     Seg<T>* tops = reinterpret_cast<Seg<T>*>(smem + YTreeSmem<T>::off_tops(threads));
     T* xtop = reinterpret_cast<T*>(smem + YTreeSmem<T>::off_xtop(threads, n_slots, G));
     const int q = gq - rank * tcol;
+    Node<T> ndc;
     {
       Seg<T> S;
-      chunk_reduce<K, T>(d, s, S.f, S.l);
+      chunk_reduce_split<K, T>(d, s, S, ndc);
       csum[col * tcol + q] = S;
     }
     __syncthreads();
@@ -238,7 +245,7 @@ __device__ __forceinline__ void y_solve_cols(unsigned char* smem, int log2W, int
       const T* src = cl.map_shared_rank(xtop + 2 * (t_slot * G + gg), t_owner);
       xa = src[0];
       xc = src[1];
-      cl.sync();  // owners keep their shared memory until every read is done
+      if (final_sync) cl.sync();  // owners keep their shared memory until every read is done
     } else {
       __syncthreads();
       xa = xtop[2 * (t_slot * G + gg)];
@@ -251,7 +258,7 @@ __device__ __forceinline__ void y_solve_cols(unsigned char* smem, int log2W, int
     cx[1] = xc;
     __syncthreads();
     const T* mine = reinterpret_cast<const T*>(csum + col * tcol + q);
-    chunk_backsub<K, T>(d, s, mine[0], mine[1]);
+    chunk_backsub_split<K, T>(d, s, ndc, mine[0], mine[1]);
   } else {
     const int N = (2 * C) << log2tcol;
     int log2N = log2tcol + 1;
