@@ -365,8 +365,9 @@ __device__ __forceinline__ void pcr64(Eq<T>& E0, Eq<T>& E1, int lane, int n_eq) 
     E0 = n0;
     E1 = n1;
   }
-  // distances 2, 4, ..., 32 (lane offsets 1, 2, ..., 16)
-  for (int h = 1; h < 32; h <<= 1) {
+  // distances 2, 4, ..., 32 (lane offsets 1, 2, ..., 16); a level is needed
+  // only while the coupling distance 2h is below the number of equations
+  for (int h = 1; h < 32 && 2 * h < n_eq; h <<= 1) {
     const int s = 2 * h;
     Eq<T> lo0 = shfl_up_eq(E0, h), lo1 = shfl_up_eq(E1, h);
     Eq<T> hi0 = shfl_down_eq(E0, h), hi1 = shfl_down_eq(E1, h);

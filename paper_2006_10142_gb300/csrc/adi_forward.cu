@@ -622,9 +622,11 @@ cudaError_t launch_x_pipe(const XArgs& a, int K, const CUtensorMap& tu, const CU
   return cudaErrorInvalidValue;
 }
 
+static size_t y_pipe_tree_bytes(int C, int tcol) { return y_smem_bytes(16, C, tcol, false, true); }
+
 size_t y_pipe_smem_bytes(int C, int tcol, int K) {
   const size_t R = (size_t)tcol * K;
-  return align64(y_smem_bytes(16, C, tcol, false, true)) + 8 + 128 + 2 * R * 16 * 4;
+  return align64(y_pipe_tree_bytes(C, tcol)) + 8 + 128 + 2 * R * 16 * 4;
 }
 
 int y_pipe_box_rows(int tcol, int K) {
@@ -656,7 +658,7 @@ static cudaError_t launch_y_pipe_t(const YArgs& a_in, const YMaps& mp, cudaStrea
   const int tcol = 1 << a.log2tcol;
   const int threads = 16 * tcol;
   if (a.log2W != 4 || threads % 32 != 0 || threads > MAXT || tcol * K < 64) return cudaErrorInvalidValue;
-  a.stage_off = (int)align64(y_smem_bytes(16, a.C, tcol, false, true));
+  a.stage_off = (int)align64(y_pipe_tree_bytes(a.C, tcol));
   const size_t sm = y_pipe_smem_bytes(a.C, tcol, K);
   if (sm > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
   const int strips = (a.nx + 15) / 16;
