@@ -17,7 +17,8 @@
 //   (tau^2/2) Lap_y z = (z - w)/m,  (tau^2/2) Lap_x w = (w - r)/m,
 //   tau^2 Lap u^k = (r - tau^2 f)/m,
 // so  dJ/dm += (wbar (z - w) + rbar (w - tau^2 f)) / m,
-// accumulated in FP64.
+// each step's increment formed in FP32 from the FP32 fields and accumulated
+// over the steps in FP64.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -27,9 +28,15 @@
 
 namespace adi {
 
-// Y^T wbar = lam (column solves): d = m . lam, solve with Y, wbar = x / m.
+// MAXT bounds the CTA size: 1024 caps a thread at 64 registers, 512 at 128,
+// 256 at 128 with two CTAs per SM (the launchers pick the smallest bound
+// that holds the CTA).
+constexpr int adj_min_ctas(int maxt) { return maxt <= 256 ? 2 : 1; }
+
+// Y^T wbar = lam (column solves): d = m . lam, solve with Y, wbar = x / m
+// (m is read again for the division rather than kept in registers).
 template <int K, typename T, int MAXT>
-__global__ void __launch_bounds__(MAXT, 1) y_adj_kernel(const YAdjArgs a) {
+__global__ void __launch_bounds__(MAXT, adj_min_ctas(MAXT)) y_adj_kernel(const YAdjArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int W = 1 << a.log2W;
   const int tcol = 1 << a.log2tcol;
@@ -45,28 +52,39 @@ __global__ void __launch_bounds__(MAXT, 1) y_adj_kernel(const YAdjArgs a) {
   const int j0 = gq * K;
   const bool colok = i < a.nx;
   const T sc = (T)a.sc;
-  T d[K], s[K], mm[K];
+  const size_t ld = (size_t)a.ld;
+  const size_t base = (size_t)j0 * ld + i;
+  const bool full = colok && j0 + K <= a.ny;
+  T d[K], s[K];
+  if (full) {
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const int r = j0 + k;
-    const bool ok = colok && r < a.ny;
-    const size_t idx = (size_t)r * a.ld + i;
-    mm[k] = ok ? (T)__ldg(a.m + idx) : T(1);
-    d[k] = ok ? mm[k] * (T)__ldg(a.lam + idx) : T(0);
-    s[k] = ok ? sc * mm[k] : T(0);
+    for (int k = 0; k < K; ++k) {
+      const T mk = (T)__ldg(a.m + base + k * ld);
+      d[k] = mk * (T)__ldg(a.lam + base + k * ld);
+      s[k] = sc * mk;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const bool ok = colok && j0 + k < a.ny;
+      const T mk = ok ? (T)__ldg(a.m + base + k * ld) : T(1);
+      d[k] = ok ? mk * (T)__ldg(a.lam + base + k * ld) : T(0);
+      s[k] = ok ? sc * mk : T(0);
+    }
   }
   y_solve_cols<K, T, true>(smem, a.log2W, a.log2tcol, C, rank, a.pcr, col, gq, d, s);
+  if (colok) {
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const int r = j0 + k;
-    if (colok && r < a.ny) a.wbar[(size_t)r * a.ld + i] = (float)(d[k] / mm[k]);
+    for (int k = 0; k < K; ++k)
+      if (j0 + k < a.ny) a.wbar[base + k * ld] = (float)(d[k] / (T)__ldg(a.m + base + k * ld));
   }
 }
 
 // X^T rbar = wbar (row solves) fused with the FP64 gradient accumulation and
-// the wavelet gradient at the source node.
+// the wavelet gradient at the source node (four unknowns at a time after
+// the solve, to keep registers for the solver).
 template <int K, typename T, int MAXT>
-__global__ void __launch_bounds__(MAXT, 1) x_adj_kernel(const XAdjArgs a) {
+__global__ void __launch_bounds__(MAXT, adj_min_ctas(MAXT)) x_adj_kernel(const XAdjArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tsys = 1 << a.log2tsys;
   const int tid = threadIdx.x;
@@ -94,28 +112,33 @@ __global__ void __launch_bounds__(MAXT, 1) x_adj_kernel(const XAdjArgs a) {
   }
   x_solve_rows<K, T, true>(smem, a.spc, a.log2tsys, a.pcr, sys, p, d, s);
   if (!active) return;
-  float mv[K], wb[K], wf[K], zf[K];
-  load_vec<K>(mv, a.m + row + i0);
-  load_vec<K>(wb, a.wbar + row + i0);
-  load_vec<K>(wf, a.w + row + i0);
-  load_vec<K>(zf, a.z + row + i0);
-  float rb[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) rb[k] = ((i0 + k) < a.nx) ? (float)(d[k] / (T)mv[k]) : 0.f;
-  store_vec<K, float>(a.rbar + row + i0, rb);
   const bool has_src = (j == a.src_iy) && a.src_ix >= i0 && a.src_ix < i0 + K;
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    if ((i0 + k) >= a.nx) continue;
-    const double r_ = (double)d[k] / (double)mv[k];
-    double wsrc = (double)wf[k];
-    if (has_src && i0 + k == a.src_ix && a.wavelet != nullptr && a.level >= 0 &&
-        a.level < a.n_wavelet)
-      wsrc -= a.src_scale * (double)a.wavelet[a.level];  // tau^2 f^k at the source
-    const double inc = ((double)wb[k] * ((double)zf[k] - (double)wf[k]) + r_ * wsrc) / (double)mv[k];
-    a.gm[(size_t)j * a.nx + i0 + k] += inc;
-    if (has_src && i0 + k == a.src_ix && a.gw != nullptr && a.level >= 0 && a.level < a.n_wavelet)
-      a.gw[a.level] += (float)(a.src_scale * r_);
+  for (int c = 0; c < K / 4; ++c) {
+    const int e = i0 + 4 * c;
+    float mv[4], wb[4], wf[4], zf[4], rb[4];
+    load_vec<4>(mv, a.m + row + e);
+    load_vec<4>(wb, a.wbar + row + e);
+    load_vec<4>(wf, a.w + row + e);
+    load_vec<4>(zf, a.z + row + e);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) rb[k] = (e + k < a.nx) ? (float)(d[4 * c + k] / (T)mv[k]) : 0.f;
+    store_vec<4, float>(a.rbar + row + e, rb);
+    // the step's increment is formed in FP32 (its inputs are FP32 fields);
+    // the running sum over all steps is FP64 (one FP64 add per node)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (e + k >= a.nx) continue;
+      const float r_ = rb[k];
+      float wsrc = wf[k];
+      if (has_src && e + k == a.src_ix && a.wavelet != nullptr && a.level >= 0 &&
+          a.level < a.n_wavelet)
+        wsrc -= (float)(a.src_scale * (double)a.wavelet[a.level]);  // tau^2 f^k at the source
+      const float inc = (wb[k] * (zf[k] - wf[k]) + r_ * wsrc) / mv[k];
+      a.gm[(size_t)j * a.nx + e + k] += (double)inc;
+      if (has_src && e + k == a.src_ix && a.gw != nullptr && a.level >= 0 && a.level < a.n_wavelet)
+        a.gw[a.level] += (float)(a.src_scale * (double)r_);
+    }
   }
 }
 
@@ -194,6 +217,7 @@ static cudaError_t launch_ya_t(const YAdjArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_x_adj(const XAdjArgs& a, int K, bool fp64, cudaStream_t st) {
+  const int threads = a.spc << a.log2tsys;
   if (fp64) {
     switch (K) {
       case 4: return launch_xa_t<4, double, 512>(a, st);
@@ -205,14 +229,21 @@ cudaError_t launch_x_adj(const XAdjArgs& a, int K, bool fp64, cudaStream_t st) {
     switch (K) {
       case 4: return launch_xa_t<4, float, 1024>(a, st);
       case 8: return launch_xa_t<8, float, 1024>(a, st);
-      case 16: return launch_xa_t<16, float, 1024>(a, st);
-      case 32: return launch_xa_t<32, float, 1024>(a, st);
+      case 16:
+        if (threads <= 256) return launch_xa_t<16, float, 256>(a, st);
+        if (threads <= 512) return launch_xa_t<16, float, 512>(a, st);
+        return launch_xa_t<16, float, 1024>(a, st);
+      case 32:
+        if (threads <= 256) return launch_xa_t<32, float, 256>(a, st);
+        if (threads <= 512) return launch_xa_t<32, float, 512>(a, st);
+        return launch_xa_t<32, float, 1024>(a, st);
     }
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_y_adj(const YAdjArgs& a, int K, bool fp64, cudaStream_t st) {
+  const int threads = 1 << (a.log2W + a.log2tcol);
   if (fp64) {
     switch (K) {
       case 4: return launch_ya_t<4, double, 512>(a, st);
@@ -224,8 +255,14 @@ cudaError_t launch_y_adj(const YAdjArgs& a, int K, bool fp64, cudaStream_t st) {
     switch (K) {
       case 4: return launch_ya_t<4, float, 1024>(a, st);
       case 8: return launch_ya_t<8, float, 1024>(a, st);
-      case 16: return launch_ya_t<16, float, 1024>(a, st);
-      case 32: return launch_ya_t<32, float, 1024>(a, st);
+      case 16:
+        if (threads <= 256) return launch_ya_t<16, float, 256>(a, st);
+        if (threads <= 512) return launch_ya_t<16, float, 512>(a, st);
+        return launch_ya_t<16, float, 1024>(a, st);
+      case 32:
+        if (threads <= 256) return launch_ya_t<32, float, 256>(a, st);
+        if (threads <= 512) return launch_ya_t<32, float, 512>(a, st);
+        return launch_ya_t<32, float, 1024>(a, st);
     }
   }
   return cudaErrorInvalidValue;
@@ -278,6 +315,14 @@ cudaError_t configure_adjoint_kernels() {
   ADI_CFG((y_adj_kernel<8, double, 512>))
   ADI_CFG((y_adj_kernel<16, double, 512>))
   ADI_CFG((y_adj_kernel<32, double, 512>))
+  ADI_CFG((x_adj_kernel<16, float, 256>))
+  ADI_CFG((x_adj_kernel<16, float, 512>))
+  ADI_CFG((x_adj_kernel<32, float, 256>))
+  ADI_CFG((x_adj_kernel<32, float, 512>))
+  ADI_CFG((y_adj_kernel<16, float, 256>))
+  ADI_CFG((y_adj_kernel<16, float, 512>))
+  ADI_CFG((y_adj_kernel<32, float, 256>))
+  ADI_CFG((y_adj_kernel<32, float, 512>))
 #undef ADI_CFG
   return e;
 }
