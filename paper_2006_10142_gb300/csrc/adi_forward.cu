@@ -308,7 +308,13 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
     }
   };
   int strip = blockIdx.x / C;
-  if (tid < 32 && strip < nstrips) issue(strip);
+  if (tid < 32) {
+    if (lane == 0) prefetch_tensormap(&tm_w);
+    if (lane == 1) prefetch_tensormap(&tm_m);
+    if (lane == 2) prefetch_tensormap(&tm_uc);
+    if (lane == 3) prefetch_tensormap(&tm_up);
+    if (strip < nstrips) issue(strip);
+  }
   const int col = tid & (W - 1);
   const int q = tid >> 4;
   const int gq = rank * tcol + q;
@@ -323,12 +329,22 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
     const bool colok = i < a.nx;
     if (!mbar_wait_bounded(bar, phase, 1000000000ull)) timed_out = true;
     phase ^= 1u;
+    // Rows k and K-1-k are read as a pair; odd q-groups (lanes 16..31) take
+    // them in the opposite order, so that at each read the two half-warps
+    // are an odd number of 64-byte rows apart: different bank halves.
     float d[K], s[K];
+    const bool flip = (q & 1) != 0;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const int o = (q * K + k) * W + col;
-      d[k] = colok ? sw[o] : 0.f;
-      s[k] = colok ? sc * smv[o] : 0.f;
+    for (int k = 0; k < K / 2; ++k) {
+      const int k2 = K - 1 - k;
+      const int o1 = (q * K + (flip ? k2 : k)) * W + col;
+      const int o2 = (q * K + (flip ? k : k2)) * W + col;
+      const float w1 = sw[o1], w2 = sw[o2];
+      const float m1 = smv[o1], m2 = smv[o2];
+      d[k] = colok ? (flip ? w2 : w1) : 0.f;
+      d[k2] = colok ? (flip ? w1 : w2) : 0.f;
+      s[k] = colok ? sc * (flip ? m2 : m1) : 0.f;
+      s[k2] = colok ? sc * (flip ? m1 : m2) : 0.f;
     }
     __syncthreads();  // the stage is consumed: refill it with the next strip
     const int next = strip + ncl;

@@ -115,6 +115,11 @@ __device__ __forceinline__ void bulk_wait_read() {
 // Wait until the committed bulk stores are complete.
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
+// Brings a tensor map (kernel parameter) into the descriptor cache.
+__device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* tm) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tm)) : "memory");
+}
+
 // Bulk (non-tensor) copy of `bytes` (a multiple of 16, both addresses
 // 16-byte aligned) from global memory into this CTA's shared memory,
 // completing on `bar`.
