@@ -146,15 +146,19 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
         K *= 2;
       }
     }
-    // FP32, long columns, CTA size not given: 32 rows per thread in CTAs of
-    // 256 threads (two per SM) when the column fits a portable cluster of
-    // them, else 512 (one per SM, up to 16 CTAs per cluster)
+    // FP32, long columns, CTA size not given: 32 rows per thread, and the
+    // largest CTA (up to 512 threads, one per SM) that still leaves at least
+    // 512 CTAs (strips x cluster size) in the grid; smaller grids get
+    // smaller CTAs rather than idle SMs
     if (cty == 0 && t.chunk_y == 0 && !P.fp64y && G.ny >= 1024) {
       const int ttot = next_pow2((G.ny + 31) / 32);
-      const int tc256 = std::max(1, 256 / W), tc512 = std::max(1, 512 / W);
+      const int strips = (G.nx + W - 1) / W;
       int tcol = 0;
-      if (ttot <= 8 * tc256) tcol = std::min(ttot, tc256);
-      else if (ttot <= maxC * tc512) tcol = tc512;
+      for (int tc = std::max(1, 512 / W); tc >= std::max(1, 64 / W); tc >>= 1) {
+        if (tc > ttot || ttot / tc > maxC) continue;
+        tcol = tc;
+        if ((long long)strips * (ttot / tc) >= 512) break;
+      }
       const int groups = tcol ? (ttot / tcol) * std::max(1, tcol / 32) : 0;
       if (tcol && (!P.tree || groups <= 32)) {
         K = 32;
@@ -170,8 +174,9 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
     if (t.y_stage < ADI_STAGE_AUTO || t.y_stage > ADI_STAGE_TMA) { why = "unknown y_stage"; return ADI_EINVAL; }
     int stage = t.y_stage;
     // pipelined strips: FP32 tree solver, 16 columns, K >= 16, <= 512 threads
-    const bool ypipe_ok = !P.fp64y && P.tree && W == 16 && K >= 16 && W * tcol <= 512 && tcol * K >= 64 &&
-                          y_pipe_smem_bytes(C, tcol, K) <= (size_t)kMaxDynSmem;
+    const bool ypipe_ok = !P.fp64y && P.tree && W == 16 && (K == 32 || K == 16) &&
+                          W * tcol <= 512 && W * tcol >= 32 && tcol * K >= 64 &&
+                          y_pipe_smem_bytes(W, C, tcol, K) <= (size_t)kMaxDynSmem;
     if (stage == ADI_STAGE_TMA && !ypipe_ok) { why = "y pipeline not available for this shape"; return ADI_EUNSUPPORTED; }
     if (stage == ADI_STAGE_AUTO && ypipe_ok) stage = ADI_STAGE_TMA;
     if (stage == ADI_STAGE_AUTO) {

@@ -253,23 +253,24 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT)) y_sweep_kernel(const YAr
 }
 
 // ---------------------------------------------------------------------------
-// pass 2, pipelined form (FP32, tree solver, strips of 16 columns):
-// persistent clusters loop over strips; while one strip is solved, each CTA
-// loads its rows of the next strip's w and m into shared memory with TMA
-// tensor boxes of 16 columns x BH rows (completing on an mbarrier) and
-// prefetches the same boxes of u^k and u^{k-1} into L2 for the update.
+// pass 2, pipelined form (FP32, tree solver, strips of W columns; launched
+// with W = 16): persistent clusters loop over strips; while one strip is
+// solved, each CTA loads its rows of the next strip's w and m into shared
+// memory with TMA tensor boxes of W columns x BH rows (completing on an
+// mbarrier) and prefetches the same boxes of u^k and u^{k-1} into L2 for the
+// update.
 // Shared memory: [solver region] [mbarrier at a.stage_off] [pad to 128 B]
-// [w tile] [m tile], each R x 16 floats, R = tcol * K rows of this CTA.
+// [w tile] [m tile], each R x W floats, R = tcol * K rows of this CTA.
 // Rows beyond ny and columns beyond the row pitch arrive as zeros; columns
 // beyond nx are masked.
 // ---------------------------------------------------------------------------
-template <int K, int MAXT>
+template <int K, int MAXT, int W>
 __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
     y_pipe_kernel(const YArgs a, const __grid_constant__ CUtensorMap tm_w,
                   const __grid_constant__ CUtensorMap tm_m, const __grid_constant__ CUtensorMap tm_uc,
                   const __grid_constant__ CUtensorMap tm_up) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int W = 16;
+  constexpr int QG = 32 / W;  // row groups (q) per warp
   const int C = a.C;
   const int rank = cluster_rank(C);
   const int tid = threadIdx.x;
@@ -316,7 +317,8 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
     if (strip < nstrips) issue(strip);
   }
   const int col = tid & (W - 1);
-  const int q = tid >> 4;
+  const int q = tid / W;
+  const int qq = q & (QG - 1);  // this thread's row group within its warp
   const int gq = rank * tcol + q;
   const int j0 = gq * K;
   uint32_t phase = 0;
@@ -329,22 +331,39 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
     const bool colok = i < a.nx;
     if (!mbar_wait_bounded(bar, phase, 1000000000ull)) timed_out = true;
     phase ^= 1u;
-    // Rows k and K-1-k are read as a pair; odd q-groups (lanes 16..31) take
-    // them in the opposite order, so that at each read the two half-warps
-    // are an odd number of 64-byte rows apart: different bank halves.
+    // Rows are read in blocks of QG: row group qq takes row g + (i ^ qq) at
+    // read i, so the QG groups of a warp read rows that differ modulo QG,
+    // i.e. different 4W-byte slots of a 128-byte bank row (conflict-free);
+    // a butterfly of selects on the bits of qq puts the values back in order.
     float d[K], s[K];
-    const bool flip = (q & 1) != 0;
 #pragma unroll
-    for (int k = 0; k < K / 2; ++k) {
-      const int k2 = K - 1 - k;
-      const int o1 = (q * K + (flip ? k2 : k)) * W + col;
-      const int o2 = (q * K + (flip ? k : k2)) * W + col;
-      const float w1 = sw[o1], w2 = sw[o2];
-      const float m1 = smv[o1], m2 = smv[o2];
-      d[k] = colok ? (flip ? w2 : w1) : 0.f;
-      d[k2] = colok ? (flip ? w1 : w2) : 0.f;
-      s[k] = colok ? sc * (flip ? m2 : m1) : 0.f;
-      s[k2] = colok ? sc * (flip ? m1 : m2) : 0.f;
+    for (int g = 0; g < K; g += QG) {
+      float vw[QG], vm[QG];
+#pragma unroll
+      for (int i = 0; i < QG; ++i) {
+        const int o = (q * K + g + (i ^ qq)) * W + col;
+        vw[i] = sw[o];
+        vm[i] = smv[o];
+      }
+#pragma unroll
+      for (int b = 1; b < QG; b <<= 1) {
+        const bool x = (qq & b) != 0;
+#pragma unroll
+        for (int i = 0; i < QG; ++i) {
+          if ((i & b) == 0) {
+            const float w0 = vw[i], w1 = vw[i | b], m0 = vm[i], m1 = vm[i | b];
+            vw[i] = x ? w1 : w0;
+            vw[i | b] = x ? w0 : w1;
+            vm[i] = x ? m1 : m0;
+            vm[i | b] = x ? m0 : m1;
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < QG; ++i) {
+        d[g + i] = colok ? vw[i] : 0.f;
+        s[g + i] = colok ? sc * vm[i] : 0.f;
+      }
     }
     __syncthreads();  // the stage is consumed: refill it with the next strip
     const int next = strip + ncl;
@@ -638,11 +657,11 @@ cudaError_t launch_x_pipe(const XArgs& a, int K, const CUtensorMap& tu, const CU
   return cudaErrorInvalidValue;
 }
 
-static size_t y_pipe_tree_bytes(int C, int tcol) { return y_smem_bytes(16, C, tcol, false, true); }
+static size_t y_pipe_tree_bytes(int W, int C, int tcol) { return y_smem_bytes(W, C, tcol, false, true); }
 
-size_t y_pipe_smem_bytes(int C, int tcol, int K) {
+size_t y_pipe_smem_bytes(int W, int C, int tcol, int K) {
   const size_t R = (size_t)tcol * K;
-  return align64(y_pipe_tree_bytes(C, tcol)) + 8 + 128 + 2 * R * 16 * 4;
+  return align64(y_pipe_tree_bytes(W, C, tcol)) + 8 + 128 + 2 * R * W * 4;
 }
 
 int y_pipe_box_rows(int tcol, int K) {
@@ -651,16 +670,18 @@ int y_pipe_box_rows(int tcol, int K) {
 }
 
 // Tensor map of a pitched [ny][ld] FP32 field as 2D {ld, ny}, boxes of
-// {16, box_rows}, no swizzle, zero fill outside.
-cudaError_t encode_strip_map(CUtensorMap* out, const float* base, int ld, int ny, int box_rows) {
+// {box_cols, box_rows} (box_cols = 4, 8 or 16), no swizzle, zero fill outside.
+cudaError_t encode_strip_map(CUtensorMap* out, const float* base, int ld, int ny, int box_cols,
+                             int box_rows) {
   EncodeTiledFn fn = nullptr;
   cudaError_t e = get_encode_fn(&fn);
   if (e != cudaSuccess) return e;
-  if (ld % 32 != 0 || box_rows < 1 || box_rows > 256 || ((uintptr_t)base & 15) != 0)
+  if (ld % 32 != 0 || box_rows < 1 || box_rows > 256 || ((uintptr_t)base & 15) != 0 ||
+      (box_cols != 4 && box_cols != 8 && box_cols != 16))
     return cudaErrorInvalidValue;
   const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)ny};
   const cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
-  const cuuint32_t box[2] = {16, (cuuint32_t)box_rows};
+  const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   const cuuint32_t es[2] = {1, 1};
   const CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims,
                         strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -668,16 +689,16 @@ cudaError_t encode_strip_map(CUtensorMap* out, const float* base, int ld, int ny
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int K, int MAXT>
+template <int K, int MAXT, int W>
 static cudaError_t launch_y_pipe_t(const YArgs& a_in, const YMaps& mp, cudaStream_t st) {
   YArgs a = a_in;
   const int tcol = 1 << a.log2tcol;
-  const int threads = 16 * tcol;
-  if (a.log2W != 4 || threads % 32 != 0 || threads > MAXT || tcol * K < 64) return cudaErrorInvalidValue;
-  a.stage_off = (int)align64(y_pipe_tree_bytes(a.C, tcol));
-  const size_t sm = y_pipe_smem_bytes(a.C, tcol, K);
+  const int threads = W * tcol;
+  if ((1 << a.log2W) != W || threads % 32 != 0 || threads > MAXT || tcol * K < 64) return cudaErrorInvalidValue;
+  a.stage_off = (int)align64(y_pipe_tree_bytes(W, a.C, tcol));
+  const size_t sm = y_pipe_smem_bytes(W, a.C, tcol, K);
   if (sm > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
-  const int strips = (a.nx + 15) / 16;
+  const int strips = (a.nx + W - 1) / W;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(strips * a.C, 1, 1);
   cfg.blockDim = dim3(threads, 1, 1);
@@ -691,16 +712,20 @@ static cudaError_t launch_y_pipe_t(const YArgs& a_in, const YMaps& mp, cudaStrea
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int nc = 0;
-  cudaError_t e = cudaOccupancyMaxActiveClusters(&nc, y_pipe_kernel<K, MAXT>, &cfg);
+  cudaError_t e = cudaOccupancyMaxActiveClusters(&nc, y_pipe_kernel<K, MAXT, W>, &cfg);
   if (e != cudaSuccess) return e;
   cfg.gridDim = dim3(std::max(1, std::min(strips, nc)) * a.C, 1, 1);
-  return cudaLaunchKernelEx(&cfg, y_pipe_kernel<K, MAXT>, a, mp.w, mp.m, mp.uc, mp.up);
+  return cudaLaunchKernelEx(&cfg, y_pipe_kernel<K, MAXT, W>, a, mp.w, mp.m, mp.uc, mp.up);
 }
 
+// 16-column strips (narrower strips, which fit smaller clusters, measured
+// far slower: their TMA boxes and row segments are 16 or 32 bytes wide).
 cudaError_t launch_y_pipe(const YArgs& a, int K, const YMaps& mp, cudaStream_t st) {
   const int threads = 1 << (a.log2W + a.log2tcol);
-  if (K == 16) return threads <= 256 ? launch_y_pipe_t<16, 256>(a, mp, st) : launch_y_pipe_t<16, 512>(a, mp, st);
-  if (K == 32) return threads <= 256 ? launch_y_pipe_t<32, 256>(a, mp, st) : launch_y_pipe_t<32, 512>(a, mp, st);
+  const int W = 1 << a.log2W;
+  const bool small = threads <= 256;
+  if (K == 16 && W == 16) return small ? launch_y_pipe_t<16, 256, 16>(a, mp, st) : launch_y_pipe_t<16, 512, 16>(a, mp, st);
+  if (K == 32 && W == 16) return small ? launch_y_pipe_t<32, 256, 16>(a, mp, st) : launch_y_pipe_t<32, 512, 16>(a, mp, st);
   return cudaErrorInvalidValue;
 }
 
@@ -785,10 +810,10 @@ cudaError_t configure_kernels() {
   ADI_CFG_SMALL(x_sweep_kernel, false, false)
   ADI_CFG_SMALL(y_sweep_kernel, true, true)
   ADI_CFG_SMALL(y_sweep_kernel, false, true)
-  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<16, 256>, true);
-  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<16, 512>, true);
-  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<32, 256>, true);
-  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<32, 512>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<16, 256, 16>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<16, 512, 16>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<32, 256, 16>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<32, 512, 16>, true);
   if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<8, 1024>, false);
   if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<16, 256>, false);
   if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<16, 512>, false);

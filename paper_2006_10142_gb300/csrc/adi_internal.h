@@ -79,9 +79,10 @@ size_t y_stage_bytes(int threads, int K);
 size_t x_stage_bytes(int threads, int K);
 size_t x_pipe_smem_bytes(int spc, int tsys, int K);
 int x_pipe_box_lines(int tsys, int K);
-size_t y_pipe_smem_bytes(int C, int tcol, int K);
+size_t y_pipe_smem_bytes(int W, int C, int tcol, int K);
 int y_pipe_box_rows(int tcol, int K);
-cudaError_t encode_strip_map(CUtensorMap* out, const float* base, int ld, int ny, int box_rows);
+cudaError_t encode_strip_map(CUtensorMap* out, const float* base, int ld, int ny, int box_cols,
+                             int box_rows);
 // Strip maps of the pipelined y sweep: w, m, u^k, u^{k-1}.
 struct YMaps {
   CUtensorMap w, m, uc, up;

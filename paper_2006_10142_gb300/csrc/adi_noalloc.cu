@@ -185,11 +185,12 @@ extern "C" int adi_wave_step_noalloc(const adi_wave_desc* desc, int32_t ld, doub
   if (e != cudaSuccess) return fail_msg(ADI_ECUDA, std::string("x sweep launch: ") + cudaGetErrorString(e));
   if (P.y_stage == 3) {
     const int BH = y_pipe_box_rows(1 << P.log2tcol, P.ky);
+    const int BW = 1 << P.log2W;
     YMaps mp;
-    e = encode_strip_map(&mp.w, slot->w, ld, d.ny, BH);
-    if (e == cudaSuccess) e = encode_strip_map(&mp.m, m, ld, d.ny, BH);
-    if (e == cudaSuccess) e = encode_strip_map(&mp.uc, u_cur, ld, d.ny, BH);
-    if (e == cudaSuccess) e = encode_strip_map(&mp.up, u_prev, ld, d.ny, BH);
+    e = encode_strip_map(&mp.w, slot->w, ld, d.ny, BW, BH);
+    if (e == cudaSuccess) e = encode_strip_map(&mp.m, m, ld, d.ny, BW, BH);
+    if (e == cudaSuccess) e = encode_strip_map(&mp.uc, u_cur, ld, d.ny, BW, BH);
+    if (e == cudaSuccess) e = encode_strip_map(&mp.up, u_prev, ld, d.ny, BW, BH);
     if (e != cudaSuccess) return fail_msg(ADI_ECUDA, std::string("strip maps: ") + cudaGetErrorString(e));
     e = launch_y_pipe(ya, P.ky, mp, st);
   } else {

@@ -330,12 +330,13 @@ int adi_wave::launch_fwd(Grid& G, const float* u_cur, float* u_prev, float* w, f
   if (profile && prof_begin(st, &a) != ADI_OK) return ADI_ECUDA;
   if (P.y_stage == 3) {
     const int BH = y_pipe_box_rows(1 << P.log2tcol, P.ky);
-    if (G.ts_rows != BH) {
-      CK(encode_strip_map(&G.ts_buf[0], G.buf[0], G.ld, G.ny, BH), "strip map u0");
-      CK(encode_strip_map(&G.ts_buf[1], G.buf[1], G.ld, G.ny, BH), "strip map u1");
-      CK(encode_strip_map(&G.ts_m, G.m, G.ld, G.ny, BH), "strip map m");
-      CK(encode_strip_map(&G.ts_w, G.w, G.ld, G.ny, BH), "strip map w");
-      G.ts_rows = BH;
+    const int BW = 1 << P.log2W;
+    if (G.ts_rows != BH * 64 + BW) {
+      CK(encode_strip_map(&G.ts_buf[0], G.buf[0], G.ld, G.ny, BW, BH), "strip map u0");
+      CK(encode_strip_map(&G.ts_buf[1], G.buf[1], G.ld, G.ny, BW, BH), "strip map u1");
+      CK(encode_strip_map(&G.ts_m, G.m, G.ld, G.ny, BW, BH), "strip map m");
+      CK(encode_strip_map(&G.ts_w, G.w, G.ld, G.ny, BW, BH), "strip map w");
+      G.ts_rows = BH * 64 + BW;
     }
     YMaps mp;
     mp.m = G.ts_m;
@@ -346,7 +347,7 @@ int adi_wave::launch_fwd(Grid& G, const float* u_cur, float* u_prev, float* w, f
       if (p == G.w) *outm[f] = G.ts_w;
       else if (p == G.buf[0]) *outm[f] = G.ts_buf[0];
       else if (p == G.buf[1]) *outm[f] = G.ts_buf[1];
-      else CK(encode_strip_map(outm[f], p, G.ld, G.ny, BH), "strip map");
+      else CK(encode_strip_map(outm[f], p, G.ld, G.ny, BW, BH), "strip map");
     }
     CK(launch_y_pipe(ya, P.ky, mp, st), "y sweep launch");
   } else {

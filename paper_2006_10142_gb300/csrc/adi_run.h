@@ -48,7 +48,7 @@ struct Grid {
   CUtensorMap tm_buf[2], tm_m, tm_w;  // row maps of buf[0], buf[1], m, w (pipelined x sweep)
   int tm_lines = 0;                 // box height they were encoded with, 0 = none
   CUtensorMap ts_buf[2], ts_m, ts_w;  // strip maps (pipelined y sweep)
-  int ts_rows = 0;                  // box rows they were encoded with, 0 = none
+  int ts_rows = 0;                  // 64 * box rows + box columns they were encoded with, 0 = none
 };
 
 // What adi_wave_adjoint needs to replay the last run.
