@@ -75,9 +75,9 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
     const int maxT = std::min(P.fp64x ? 512 : 1024, ct ? ct : 1024);
     int K = t.chunk_x;
     if (K == 0) K = P.fp64x ? 8 : (G.nx >= 512 ? 16 : (G.nx >= 64 ? 8 : 4));
-    // FP32 rows that fit 256 threads at 32 unknowns each: longer chunks win
-    // (fewer interface equations per row, two CTAs per SM)
-    if (t.chunk_x == 0 && !P.fp64x && G.nx >= 1024 && next_pow2((G.nx + 31) / 32) <= std::min(maxT, 256)) K = 32;
+    // FP32 rows that fit 512 threads at 32 unknowns each: longer chunks win
+    // (fewer interface equations per row, no register spills)
+    if (t.chunk_x == 0 && !P.fp64x && G.nx >= 1024 && next_pow2((G.nx + 31) / 32) <= std::min(maxT, 512)) K = 32;
     if (K != 4 && K != 8 && K != 16 && K != 32) { why = "chunk_x must be 4, 8, 16 or 32"; return ADI_EINVAL; }
     while (next_pow2((G.nx + K - 1) / K) > maxT && K < 32) K *= 2;
     const int tsys = next_pow2((G.nx + K - 1) / K);

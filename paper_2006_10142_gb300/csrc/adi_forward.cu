@@ -66,10 +66,10 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT)) x_sweep_kernel(const XAr
 // pass 1, pipelined form (FP32, tree solver): persistent CTAs loop over row
 // blocks; while the rows of one block are solved, TMA brings the next
 // block's rows of u^k and m into shared memory, so the loads of the next
-// block overlap the solve of this one.  Halo rows come from the stage when
-// they belong to the block and from L2 otherwise (the neighbouring blocks
-// are staged by the neighbouring CTAs at about the same time; the two rows
-// just outside the next block are also prefetched into L2).
+// block overlap the solve of this one.  Halo rows (j - 1 and j + 1 of every
+// row) outside the block come from L2 -- the neighbouring blocks are staged
+// by the neighbouring CTAs at about the same time, and the two rows just
+// outside the next block are prefetched.
 //
 // Shared memory: [solver region] [mbarrier at a.stage_off] [pad to 1024 B]
 // [u rows: spc x rowf floats] [m rows: spc x rowf floats], rowf = tsys * K,
@@ -135,11 +135,51 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
   const int sys = tid >> a.log2tsys;
   const int p = tid & (tsys - 1);
   const int i0 = p * K;
+  const int threads = blockDim.x;
+  const int log2row = a.log2tsys + (31 - __clz(K));  // rowf = 1 << log2row
+  const float* hsum = reinterpret_cast<const float*>(sw4) + (size_t)sys * rowf;
+  // Halo rows: with one row per CTA and K = 32 (a thread's chunk is a whole
+  // 128-byte line, so per-thread loads would touch 32 lines per warp
+  // instruction) they are read coalesced and handed over through the w
+  // stage; otherwise each thread loads its own chunk (interior halo rows of
+  // a multi-row block come from the stage).
+  const bool coalesced_halo = (K == 32) && a.spc == 1;
   uint32_t phase = 0;
   bool timed_out = false;
   for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+   if (coalesced_halo) {
+    // The halo rows u^k_{j-1} + u^k_{j+1} of the block's rows, read with
+    // coalesced float4 loads (consecutive lanes, consecutive 16-byte groups)
+    // while the stage arrives, and handed to the solving threads through the
+    // w stage, free until this block's solution is written.
+    float4 hs[K / 4];
+#pragma unroll
+    for (int qi = 0; qi < K / 4; ++qi) {
+      const int f = qi * threads + tid;
+      const int e = f << 2;
+      const int col = e & (rowf - 1);
+      const int jr = blk * a.spc + (e >> log2row);
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (jr < a.ny && col < a.nx) {
+        if (jr > 0) v = __ldg(reinterpret_cast<const float4*>(a.u + (size_t)(jr - 1) * a.ld + col));
+        if (jr + 1 < a.ny) {
+          const float4 t = __ldg(reinterpret_cast<const float4*>(a.u + (size_t)(jr + 1) * a.ld + col));
+          v.x += t.x; v.y += t.y; v.z += t.z; v.w += t.w;
+        }
+      }
+      hs[qi] = v;
+    }
+    if (tid < 32) bulk_wait_read();  // the previous block's w stage has been read out (per-lane groups)
+    __syncthreads();
+#pragma unroll
+    for (int qi = 0; qi < K / 4; ++qi) sw4[swz4(qi * threads + tid)] = hs[qi];
     if (!mbar_wait_bounded(bar, phase, 1000000000ull)) timed_out = true;
     phase ^= 1u;
+    __syncthreads();  // the halo sums are in place
+   } else {
+    if (!mbar_wait_bounded(bar, phase, 1000000000ull)) timed_out = true;
+    phase ^= 1u;
+   }
     const int j = blk * a.spc + sys;
     const bool active = j < a.ny && i0 < a.nx;
     float d[K], s[K];
@@ -148,19 +188,23 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
       const float* ur = su + (size_t)sys * rowf;
       const float* mr = sm + (size_t)sys * rowf;
       float uc[K], v[K];
-      if (sys > 0) {
-        stage_vec<K>(d, ur - rowf, i0);
-      } else if (j > 0) {
-        load_vec<K>(d, a.u + (size_t)(j - 1) * a.ld + i0);
+      if (coalesced_halo) {
+        stage_vec<K>(d, hsum, i0);
       } else {
+        if (sys > 0) {
+          stage_vec<K>(d, ur - rowf, i0);
+        } else if (j > 0) {
+          load_vec<K>(d, a.u + (size_t)(j - 1) * a.ld + i0);
+        } else {
 #pragma unroll
-        for (int k = 0; k < K; ++k) d[k] = 0.f;
-      }
-      if (j + 1 < a.ny) {
-        if (sys + 1 < a.spc) stage_vec<K>(v, ur + rowf, i0);
-        else load_vec<K>(v, a.u + (size_t)(j + 1) * a.ld + i0);
+          for (int k = 0; k < K; ++k) d[k] = 0.f;
+        }
+        if (j + 1 < a.ny) {
+          if (sys + 1 < a.spc) stage_vec<K>(v, ur + rowf, i0);
+          else load_vec<K>(v, a.u + (size_t)(j + 1) * a.ld + i0);
 #pragma unroll
-        for (int k = 0; k < K; ++k) d[k] += v[k];
+          for (int k = 0; k < K; ++k) d[k] += v[k];
+        }
       }
       stage_vec<K>(uc, ur, i0);
       stage_vec<K>(v, mr, i0);
@@ -191,7 +235,7 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
 #pragma unroll
       for (int k = 0; k < K; ++k) { d[k] = 0.f; s[k] = 0.f; }
     }
-    if (tid < 32) bulk_wait_read();  // the previous block's w stage has been read out (per-lane groups)
+    if (!coalesced_halo && tid < 32) bulk_wait_read();  // the previous block's w stage has been read out
     __syncthreads();  // every read of the stage is done: it may be refilled
     const int next = blk + (int)gridDim.x;
     if (tid < 32 && next < nblk) {
