@@ -52,11 +52,13 @@ UNIT = "grid-point updates/s"
 # algorithmic HBM bytes per grid point per launch (FP32 fields)
 BYTES_X = 12  # read u^k, m; write w
 BYTES_Y = 20  # read w, m, u^k, u^{k-1}; write u^{k+1}
-# dram__bytes_read.sum + dram__bytes_write.sum per 16384^2 launch of the
-# dominant kernel: measured by ncu on a 4096 x 16384 grid with the same launch
-# shape (profiles/y_sweep_kernel_4096x16384.txt) and scaled by the number of
-# grid points (x 4).  Only valid for the 16384^2 workload.
-NCU_TRAFFIC = {("ricker_16384", "y_sweep_kernel"): 5277511680}
+# dram__bytes_read.sum + dram__bytes_write.sum per 16384^2 launch, measured by
+# ncu on a smaller grid with the same launch shape and scaled by the number of
+# grid points: y_pipe_kernel on 4096 x 16384 (x 4,
+# profiles/y_pipe_kernel_4096x16384.txt), x_pipe_kernel on 16384 x 2048 (x 8,
+# profiles/x_pipe_kernel_16384x2048.txt).  Only valid for the 16384^2 workload.
+NCU_TRAFFIC = {("ricker_16384", "y_pipe_kernel"): 5512502272,
+               ("ricker_16384", "x_pipe_kernel"): 2936647680}
 
 
 def measured_peak_gbs():
@@ -339,7 +341,12 @@ def run_single(ctx):
     h.profile(False)
     h.sync_status()
     value = world * n * n * ts * args.steps / (max_ms / 1e3)
-    roof = _roofline(kms, kcnt, {0: "x_sweep_kernel", 1: "y_sweep_kernel"},
+    tun = h.tuning()
+    # the kernels the plan launches: the TMA-pipelined forms (stage 3) or the
+    # one-CTA-per-tile forms
+    xname = "x_pipe_kernel" if tun.get("x_stage") == 3 else "x_sweep_kernel"
+    yname = "y_pipe_kernel" if tun.get("y_stage") == 3 else "y_sweep_kernel"
+    roof = _roofline(kms, kcnt, {0: xname, 1: yname},
                      {0: BYTES_X * n * n, 1: BYTES_Y * n * n}, args.workload)
     roof["step_gbs_32B"] = 32.0 * n * n * ts * args.steps / (max_ms / 1e3) / 1e9
 
