@@ -220,7 +220,10 @@ const char *adi_wave_last_error(const adi_wave *h);
  *                   CTAs; the next rows of u^k and m arrive in shared memory
  *                   by TMA tensor copies while the current rows are solved;
  *                   FP32 tree solver, rows of >= 256 floats); FP64
- *                   elimination always reads directly.
+ *                   elimination always reads directly;
+ * x_cluster:        ADI_STAGE_TMA only: 1 = one CTA per row, 2 = each row
+ *                   split over a cluster of two CTAs (K = 32, one row per
+ *                   CTA pair; two pairs fit an SM).
  * Zero fields mean "choose automatically". */
 enum { ADI_STAGE_AUTO = 0, ADI_STAGE_SMEM = 1, ADI_STAGE_L2 = 2, ADI_STAGE_DIRECT = 2,
        ADI_STAGE_TMA = 3 };
@@ -237,6 +240,7 @@ typedef struct {
     int32_t y_stage;
     int32_t persist;
     int32_t x_stage;
+    int32_t x_cluster;
 } adi_wave_tuning;
 
 int adi_wave_get_tuning(const adi_wave *h, adi_wave_tuning *t);

@@ -63,7 +63,8 @@ class Tuning(ctypes.Structure):
                 ("pcr_size", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("solver", ctypes.c_int32), ("cta_threads", ctypes.c_int32),
                 ("cta_threads_y", ctypes.c_int32), ("y_stage", ctypes.c_int32),
-                ("persist", ctypes.c_int32), ("x_stage", ctypes.c_int32)]
+                ("persist", ctypes.c_int32), ("x_stage", ctypes.c_int32),
+                ("x_cluster", ctypes.c_int32)]
 
 
 class AdiError(RuntimeError):

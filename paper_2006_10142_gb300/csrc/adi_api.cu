@@ -99,7 +99,12 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
     // K = 32 only up to 512 threads (register budget)
     const bool pipe_ok = !P.fp64x && P.tree && tsys * K >= 256 && K >= 8 &&
                          (K < 32 || spc * tsys <= 512) &&
-                         x_pipe_smem_bytes(spc, tsys, K) <= (size_t)kMaxDynSmem;
+                         x_pipe_smem_bytes(spc, tsys, K, 1) <= (size_t)kMaxDynSmem;
+    // a row split over a cluster of two CTAs (two pairs per SM): K = 32, one
+    // row per CTA pair, at least 256 staged floats per CTA
+    const bool pair_ok = pipe_ok && K == 32 && spc == 1 && tsys >= 16 &&
+                         x_pipe_smem_bytes(1, tsys / 2, K, 2) <= (size_t)kMaxDynSmem;
+    if (t.x_cluster < 0 || t.x_cluster > 2) { why = "x_cluster must be 0, 1 or 2"; return ADI_EINVAL; }
     const bool smem_ok = !P.fp64x &&
                          align64(x_smem_bytes(spc, tsys, P.fp64x, P.tree)) + x_stage_bytes(spc * tsys, K) <=
                              (size_t)kMaxDynSmem;
@@ -111,6 +116,16 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
       else { why = "x staging does not fit shared memory"; return ADI_EUNSUPPORTED; }
     }
     P.x_stage = xs;
+    int xc = 1;
+    if (xs == ADI_STAGE_TMA) {
+      if (t.x_cluster == 2 && !pair_ok) { why = "x_cluster = 2 needs the TMA pipeline, K = 32 and one row per CTA"; return ADI_EUNSUPPORTED; }
+      // automatic: pairs for rows of 512 threads (16384 unknowns at K = 32)
+      if (t.x_cluster == 2 || (t.x_cluster == 0 && pair_ok && tsys >= 512)) xc = 2;
+    } else if (t.x_cluster == 2) {
+      why = "x_cluster = 2 needs the TMA pipeline";
+      return ADI_EUNSUPPORTED;
+    }
+    P.xc = xc;
     P.kx = K;
     P.log2tsys = ilog2(tsys);
     P.spc = spc;
@@ -343,6 +358,7 @@ extern "C" int adi_wave_get_tuning(const adi_wave* h, adi_wave_tuning* t) {
   t->y_stage = P.y_stage;
   t->persist = P.persist ? 1 : -1;
   t->x_stage = P.x_stage;
+  t->x_cluster = P.xc;
   return ADI_OK;
 }
 

@@ -72,6 +72,7 @@ int adi_wave::setup_batch(cudaStream_t st) {
       xa.stage_mode = 2;
       xa.stage_off = -1;
       xa.err = nullptr;
+      xa.xc = 1;
       YArgs& ya = B.ya[c];
       ya.nx = G.nx; ya.ny = G.ny; ya.ld = G.ld;
       ya.log2W = ilog2(W); ya.log2tcol = ilog2(tcol); ya.C = 1; ya.pcr = 32;

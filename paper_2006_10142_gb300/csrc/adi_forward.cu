@@ -88,7 +88,9 @@ __device__ __forceinline__ float stage_at(const float* row, int e) {
   return row[(swz4(e >> 2) << 2) | (e & 3)];
 }
 
-template <int K, int MAXT>
+// XC = 2: each row is split over a cluster of two CTAs (rank r stages and
+// solves columns [r rowf, (r + 1) rowf)); one row per CTA pair.
+template <int K, int MAXT, int XC>
 __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
     x_pipe_kernel(const XArgs a, const __grid_constant__ CUtensorMap tm_u,
                   const __grid_constant__ CUtensorMap tm_m, const __grid_constant__ CUtensorMap tm_w) {
@@ -96,8 +98,10 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
   constexpr int NQ = K / 4;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  const int tsys = 1 << a.log2tsys;
+  const int rank = XC == 2 ? cluster_rank(2) : 0;
+  const int tsys = 1 << a.log2tsys;        // threads per row in this CTA
   const int rowf = tsys * K;               // floats per staged row (a power of two >= 256)
+  const int coff = rank * rowf;            // first column of this CTA's part of the row
   const int lines = rowf >> 5;             // 128-byte lines per staged row
   const int L = lines < 256 ? lines : 256; // lines per TMA box
   const int nchunk = lines / L;
@@ -110,7 +114,9 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
   const float* sm = su + (size_t)a.spc * rowf;
   float4* sw4 = reinterpret_cast<float4*>(smem + (st_w - sa));
   const int nblk = (a.ny + a.spc - 1) / a.spc;
-  const uint32_t pf_bytes = (uint32_t)((a.nx * 4 + 15) & ~15);
+  // L2 prefetch of halo rows: this CTA's part of the row, inside the pitch
+  const uint32_t pf_bytes =
+      XC == 2 ? (uint32_t)(min(rowf, a.ld - coff) * 4) : (uint32_t)((a.nx * 4 + 15) & ~15);
 
   if (tid == 0) {
     mbar_init(bar, 1);
@@ -126,15 +132,18 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
       const int f = t & 1, rc = t >> 1;
       const int r = rc / nchunk, c = rc - r * nchunk;
       const uint32_t off = (uint32_t)((r * rowf + c * L * 32) * 4);
-      if (f == 0) tma_load_3d(st_u + off, &tm_u, 0, c * L, j0 + r, bar);
-      else tma_load_3d(st_m + off, &tm_m, 0, c * L, j0 + r, bar);
+      if (f == 0) tma_load_3d(st_u + off, &tm_u, 0, c * L + rank * lines, j0 + r, bar);
+      else tma_load_3d(st_m + off, &tm_m, 0, c * L + rank * lines, j0 + r, bar);
     }
   };
-  if (tid < 32 && (int)blockIdx.x < nblk) issue(blockIdx.x);
+  const int blk0 = (int)blockIdx.x / XC;
+  const int nrun = (int)gridDim.x / XC;  // CTAs (XC = 1) or CTA pairs (XC = 2) in the grid
+  if (tid < 32 && blk0 < nblk) issue(blk0);
 
   const int sys = tid >> a.log2tsys;
   const int p = tid & (tsys - 1);
-  const int i0 = p * K;
+  const int li0 = p * K;                 // first unknown of this thread within the staged part
+  const int i0 = coff + li0;             // ... and within the row
   const int threads = blockDim.x;
   const int log2row = a.log2tsys + (31 - __clz(K));  // rowf = 1 << log2row
   const float* hsum = reinterpret_cast<const float*>(sw4) + (size_t)sys * rowf;
@@ -146,7 +155,8 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
   const bool coalesced_halo = (K == 32) && a.spc == 1;
   uint32_t phase = 0;
   bool timed_out = false;
-  for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+  for (int blk = blk0; blk < nblk; blk += nrun) {
+    if constexpr (XC == 2) cluster_arrive_early(2);
    if (coalesced_halo) {
     // The halo rows u^k_{j-1} + u^k_{j+1} of the block's rows, read with
     // coalesced float4 loads (consecutive lanes, consecutive 16-byte groups)
@@ -157,7 +167,7 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
     for (int qi = 0; qi < K / 4; ++qi) {
       const int f = qi * threads + tid;
       const int e = f << 2;
-      const int col = e & (rowf - 1);
+      const int col = coff + (e & (rowf - 1));
       const int jr = blk * a.spc + (e >> log2row);
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (jr < a.ny && col < a.nx) {
@@ -189,10 +199,10 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
       const float* mr = sm + (size_t)sys * rowf;
       float uc[K], v[K];
       if (coalesced_halo) {
-        stage_vec<K>(d, hsum, i0);
+        stage_vec<K>(d, hsum, li0);
       } else {
         if (sys > 0) {
-          stage_vec<K>(d, ur - rowf, i0);
+          stage_vec<K>(d, ur - rowf, li0);
         } else if (j > 0) {
           load_vec<K>(d, a.u + (size_t)(j - 1) * a.ld + i0);
         } else {
@@ -200,16 +210,18 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
           for (int k = 0; k < K; ++k) d[k] = 0.f;
         }
         if (j + 1 < a.ny) {
-          if (sys + 1 < a.spc) stage_vec<K>(v, ur + rowf, i0);
+          if (sys + 1 < a.spc) stage_vec<K>(v, ur + rowf, li0);
           else load_vec<K>(v, a.u + (size_t)(j + 1) * a.ld + i0);
 #pragma unroll
           for (int k = 0; k < K; ++k) d[k] += v[k];
         }
       }
-      stage_vec<K>(uc, ur, i0);
-      stage_vec<K>(v, mr, i0);
-      const float uL = (i0 > 0) ? stage_at(ur, i0 - 1) : 0.f;
-      const float uR = (i0 + K < a.nx) ? stage_at(ur, i0 + K) : 0.f;
+      stage_vec<K>(uc, ur, li0);
+      stage_vec<K>(v, mr, li0);
+      // neighbours across the split between the two CTAs of a pair come from L2
+      const size_t rowg = (size_t)j * a.ld;
+      const float uL = (i0 > 0) ? (li0 > 0 ? stage_at(ur, li0 - 1) : __ldg(a.u + rowg + i0 - 1)) : 0.f;
+      const float uR = (i0 + K < a.nx) ? (li0 + K < rowf ? stage_at(ur, li0 + K) : __ldg(a.u + rowg + i0 + K)) : 0.f;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const float c = uc[k];
@@ -237,21 +249,22 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
     }
     if (!coalesced_halo && tid < 32) bulk_wait_read();  // the previous block's w stage has been read out
     __syncthreads();  // every read of the stage is done: it may be refilled
-    const int next = blk + (int)gridDim.x;
+    const int next = blk + nrun;
     if (tid < 32 && next < nblk) {
       fence_proxy_async_smem();
       issue(next);
       if (lane == 0) {
         const int jl = next * a.spc - 1, jh = next * a.spc + a.spc;
-        if (jl >= 0) l2_prefetch_bulk(a.u + (size_t)jl * a.ld, pf_bytes);
-        if (jh < a.ny) l2_prefetch_bulk(a.u + (size_t)jh * a.ld, pf_bytes);
+        if (jl >= 0) l2_prefetch_bulk(a.u + (size_t)jl * a.ld + coff, pf_bytes);
+        if (jh < a.ny) l2_prefetch_bulk(a.u + (size_t)jh * a.ld + coff, pf_bytes);
       }
     }
-    x_solve_rows<K, float, true>(smem, a.spc, a.log2tsys, a.pcr, sys, p, d, s);
+    if constexpr (XC == 2) x_solve_row_pair<K>(smem, rank, d, s);
+    else x_solve_rows<K, float, true>(smem, a.spc, a.log2tsys, a.pcr, sys, p, d, s);
     // w through the swizzled stage, stored by TMA boxes
 #pragma unroll
     for (int c = 0; c < NQ; ++c)
-      sw4[swz4((sys * rowf + i0) / 4 + c)] = make_float4(d[4 * c + 0], d[4 * c + 1], d[4 * c + 2], d[4 * c + 3]);
+      sw4[swz4((sys * rowf + li0) / 4 + c)] = make_float4(d[4 * c + 0], d[4 * c + 1], d[4 * c + 2], d[4 * c + 3]);
     fence_proxy_async_smem();
     __syncthreads();
     if (tid < 32) {
@@ -259,12 +272,13 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
       const int nrows = min(a.spc, a.ny - j0);
       for (int t = lane; t < nrows * nchunk; t += 32) {
         const int r = t / nchunk, c = t - r * nchunk;
-        tma_store_3d(&tm_w, 0, c * L, j0 + r, st_w + (uint32_t)((r * rowf + c * L * 32) * 4));
+        tma_store_3d(&tm_w, 0, c * L + rank * lines, j0 + r, st_w + (uint32_t)((r * rowf + c * L * 32) * 4));
       }
       bulk_commit();
     }
   }
   if (tid < 32) bulk_wait_all();
+  if constexpr (XC == 2) cgx::this_cluster().sync();  // no CTA leaves while its shared memory may be written
   if (timed_out && (tid & 31) == 0 && a.err) atomicOr(a.err, ERR_TIMEOUT);
 }
 
@@ -559,8 +573,15 @@ size_t y_smem_bytes(int W, int C, int tcol, bool fp64, bool tree) {
 
 size_t y_stage_bytes(int threads, int K) { return align64((size_t)2 * K * threads * sizeof(float)); }
 size_t x_stage_bytes(int threads, int K) { return align64((size_t)2 * K * threads * sizeof(float)); }
-size_t x_pipe_smem_bytes(int spc, int tsys, int K) {
-  return align64(x_smem_bytes(spc, tsys, false, true)) + 8 + 1024 + (size_t)3 * spc * tsys * K * 4;
+// tsys = threads per row in one CTA; xc = 2: the solver region holds the
+// warp summaries of both CTAs of a pair.
+static size_t x_pipe_tree_bytes(int spc, int tsys, int xc) {
+  return xc == 2 ? XTreeSmem<float>::bytes(2 * std::max(1, spc * tsys / 32))
+                 : x_smem_bytes(spc, tsys, false, true);
+}
+
+size_t x_pipe_smem_bytes(int spc, int tsys, int K, int xc) {
+  return align64(x_pipe_tree_bytes(spc, tsys, xc)) + 8 + 1024 + (size_t)3 * spc * tsys * K * 4;
 }
 
 // Tensor map of a pitched [ny][ld] FP32 field as {32, ld/32, ny} with
@@ -663,40 +684,64 @@ static cudaError_t launch_y_t(const YArgs& a_in, cudaStream_t st) {
 
 // K = 4, 8 fit 64 registers; K = 16, 32 take the smallest bound that holds
 // `threads` (float only; FP64 kernels are bounded at 512).
-template <int K, int MAXT>
+template <int K, int MAXT, int XC>
 static cudaError_t launch_x_pipe_t(const XArgs& a_in, const CUtensorMap& tu, const CUtensorMap& tm,
                                    const CUtensorMap& tw, cudaStream_t st) {
   XArgs a = a_in;
+  if (XC == 2) {  // the plan's threads per row are split over the pair
+    if (a.spc != 1 || a.log2tsys < 6) return cudaErrorInvalidValue;
+    a.log2tsys -= 1;
+  }
   const int tsys = 1 << a.log2tsys;
   const int threads = a.spc * tsys;
   if (threads % 32 != 0 || threads > MAXT || tsys * K < 256) return cudaErrorInvalidValue;
-  a.stage_off = (int)align64(x_smem_bytes(a.spc, tsys, false, true));
-  const size_t sm = x_pipe_smem_bytes(a.spc, tsys, K);
+  a.stage_off = (int)align64(x_pipe_tree_bytes(a.spc, tsys, XC));
+  const size_t sm = x_pipe_smem_bytes(a.spc, tsys, K, XC);
   if (sm > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
   const int nblk = (a.ny + a.spc - 1) / a.spc;
-  int dev = 0, nsm = 0, per_sm = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, x_pipe_kernel<K, MAXT>, threads, sm);
+  if (XC == 1) {
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, x_pipe_kernel<K, MAXT, XC>, threads, sm);
+    if (e != cudaSuccess) return e;
+    const int blocks = std::max(1, std::min(nblk, nsm * std::max(per_sm, 1)));
+    x_pipe_kernel<K, MAXT, XC><<<blocks, threads, sm, st>>>(a, tu, tm, tw);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nblk * XC, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = XC;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nc = 0;
+  cudaError_t e = cudaOccupancyMaxActiveClusters(&nc, x_pipe_kernel<K, MAXT, XC>, &cfg);
   if (e != cudaSuccess) return e;
-  const int blocks = std::max(1, std::min(nblk, nsm * std::max(per_sm, 1)));
-  x_pipe_kernel<K, MAXT><<<blocks, threads, sm, st>>>(a, tu, tm, tw);
-  return cudaGetLastError();
+  cfg.gridDim = dim3(std::max(1, std::min(nblk, nc)) * XC, 1, 1);
+  return cudaLaunchKernelEx(&cfg, x_pipe_kernel<K, MAXT, XC>, a, tu, tm, tw);
 }
 
 cudaError_t launch_x_pipe(const XArgs& a, int K, const CUtensorMap& tu, const CUtensorMap& tm,
                           const CUtensorMap& tw, cudaStream_t st) {
   const int threads = a.spc << a.log2tsys;
+  if (a.xc == 2) return K == 32 ? launch_x_pipe_t<32, 256, 2>(a, tu, tm, tw, st) : cudaErrorInvalidValue;
   switch (K) {
-    case 8: return launch_x_pipe_t<8, 1024>(a, tu, tm, tw, st);
+    case 8: return launch_x_pipe_t<8, 1024, 1>(a, tu, tm, tw, st);
     case 16:
-      if (threads <= 256) return launch_x_pipe_t<16, 256>(a, tu, tm, tw, st);
-      if (threads <= 512) return launch_x_pipe_t<16, 512>(a, tu, tm, tw, st);
-      return launch_x_pipe_t<16, 1024>(a, tu, tm, tw, st);
+      if (threads <= 256) return launch_x_pipe_t<16, 256, 1>(a, tu, tm, tw, st);
+      if (threads <= 512) return launch_x_pipe_t<16, 512, 1>(a, tu, tm, tw, st);
+      return launch_x_pipe_t<16, 1024, 1>(a, tu, tm, tw, st);
     case 32:
-      if (threads <= 256) return launch_x_pipe_t<32, 256>(a, tu, tm, tw, st);
-      return launch_x_pipe_t<32, 512>(a, tu, tm, tw, st);
+      if (threads <= 256) return launch_x_pipe_t<32, 256, 1>(a, tu, tm, tw, st);
+      return launch_x_pipe_t<32, 512, 1>(a, tu, tm, tw, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -858,12 +903,13 @@ cudaError_t configure_kernels() {
   if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<16, 512, 16>, true);
   if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<32, 256, 16>, true);
   if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<32, 512, 16>, true);
-  if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<8, 1024>, false);
-  if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<16, 256>, false);
-  if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<16, 512>, false);
-  if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<16, 1024>, false);
-  if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<32, 256>, false);
-  if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<32, 512>, false);
+  if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<8, 1024, 1>, false);
+  if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<16, 256, 1>, false);
+  if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<16, 512, 1>, false);
+  if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<16, 1024, 1>, false);
+  if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<32, 256, 1>, false);
+  if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<32, 512, 1>, false);
+  if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<32, 256, 2>, true);
   return e;
 }
 

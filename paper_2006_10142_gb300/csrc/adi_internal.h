@@ -41,6 +41,7 @@ struct XArgs {
   int stage_mode;   // 1: rows staged through shared memory (FP32), 2: direct loads, 3: TMA pipeline
   int stage_off;    // byte offset of the staging area (set by the launcher), -1: none
   int* err;         // device error word (bounded waits), or null
+  int xc;           // TMA pipeline: 2 = each row split over a cluster of two CTAs, else 1
 };
 
 // Arguments of the y-sweep + update kernel (Eq. fr2's y operator).
@@ -77,7 +78,7 @@ size_t x_smem_bytes(int spc, int tsys, bool fp64, bool tree);
 size_t y_smem_bytes(int W, int C, int tcol, bool fp64, bool tree);
 size_t y_stage_bytes(int threads, int K);
 size_t x_stage_bytes(int threads, int K);
-size_t x_pipe_smem_bytes(int spc, int tsys, int K);
+size_t x_pipe_smem_bytes(int spc, int tsys, int K, int xc);
 int x_pipe_box_lines(int tsys, int K);
 size_t y_pipe_smem_bytes(int W, int C, int tcol, int K);
 int y_pipe_box_rows(int tcol, int K);

@@ -115,7 +115,7 @@ extern "C" int adi_wave_step_noalloc(const adi_wave_desc* desc, int32_t ld, doub
   G.hy = d.ly / (d.ny + 1);
   G.fp64mode = d.fp64_solve;
   G.mmax = m_max;
-  const adi_wave_tuning t = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const adi_wave_tuning t = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   std::string why;
   rc = plan_grid(G, t, why);
   if (rc != ADI_OK) return fail_msg(rc, why);
@@ -152,6 +152,7 @@ extern "C" int adi_wave_step_noalloc(const adi_wave_desc* desc, int32_t ld, doub
   xa.stage_mode = P.x_stage;
   xa.stage_off = -1;
   xa.err = nullptr;
+  xa.xc = P.xc;
   YArgs ya;
   ya.nx = d.nx;
   ya.ny = d.ny;
@@ -172,7 +173,7 @@ extern "C" int adi_wave_step_noalloc(const adi_wave_desc* desc, int32_t ld, doub
   ya.gd = slot->gd;
   ya.err = nullptr;
   if (P.x_stage == 3) {  // host-side tensor maps of the caller's buffers (no allocation)
-    const int L = x_pipe_box_lines(1 << P.log2tsys, P.kx);
+    const int L = x_pipe_box_lines((1 << P.log2tsys) / P.xc, P.kx);
     CUtensorMap tu, tm, tw;
     e = encode_row_map(&tu, u_cur, ld, d.ny, L);
     if (e == cudaSuccess) e = encode_row_map(&tm, m, ld, d.ny, L);

@@ -280,6 +280,7 @@ int adi_wave::launch_fwd(Grid& G, const float* u_cur, float* u_prev, float* w, f
   xa.stage_mode = P.x_stage;
   xa.stage_off = -1;
   xa.err = d_err;
+  xa.xc = P.xc;
   YArgs ya;
   ya.nx = G.nx;
   ya.ny = G.ny;
@@ -303,7 +304,7 @@ int adi_wave::launch_fwd(Grid& G, const float* u_cur, float* u_prev, float* w, f
   cudaEvent_t a = nullptr;
   if (profile && prof_begin(st, &a) != ADI_OK) return ADI_ECUDA;
   if (P.x_stage == 3) {
-    const int L = x_pipe_box_lines(1 << P.log2tsys, P.kx);
+    const int L = x_pipe_box_lines((1 << P.log2tsys) / P.xc, P.kx);
     if (G.tm_lines != L) {
       CK(encode_row_map(&G.tm_buf[0], G.buf[0], G.ld, G.ny, L), "tensor map u0");
       CK(encode_row_map(&G.tm_buf[1], G.buf[1], G.ld, G.ny, L), "tensor map u1");

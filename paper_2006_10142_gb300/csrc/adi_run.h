@@ -29,6 +29,7 @@ struct GridPlan {
   int y_stage = 1;   // 1: shared-memory staging, 2: L2 prefetch
   int persist = 0;   // 1: persistent sweeps with L2 prefetch of the next tile
   int x_stage = 2;   // 1: rows staged through shared memory, 2: direct, 3: TMA pipeline
+  int xc = 1;        // TMA pipeline: CTAs per row (1 or 2)
 };
 
 struct Grid {
@@ -95,7 +96,7 @@ struct adi_wave {
   int rec_cap = 0;
   cudaStream_t cap = nullptr;  // private stream used only for graph capture
   cudaGraphExec_t pair[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [orientation][gather]
-  adi_wave_tuning tuning = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  adi_wave_tuning tuning = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   int ckpt_every = 0;
   adi::RunRecord rr;
   adi::AdjWork aw;

@@ -294,4 +294,51 @@ __device__ __forceinline__ void y_solve_cols(unsigned char* smem, int log2W, int
   }
 }
 
+// ---------------------------------------------------------------------------
+// x (row) solve of one row split over a cluster of two CTAs (FP32, tree
+// solver): rank 0 holds the first half of the row, rank 1 the second, each
+// thread K consecutive unknowns.  Every CTA writes its warp summaries to both
+// CTAs; after one cluster barrier each CTA solves the top system (2 x warps
+// segments) itself and reads its end values locally.  The caller executes
+// cluster_arrive_early(2) once per row (the next row's wait orders this row's
+// reads of `tops` before they are overwritten) and synchronises the cluster
+// before exit.  Shared memory: XTreeSmem<float> sized for 2 x warps; at most
+// 16 warps per CTA.
+// ---------------------------------------------------------------------------
+template <int K>
+__device__ __forceinline__ void x_solve_row_pair(unsigned char* smem, int rank, float (&d)[K],
+                                                 float (&s)[K]) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  Node<float>* nodes = reinterpret_cast<Node<float>*>(smem) + warp * 31;
+  Seg<float>* tops = reinterpret_cast<Seg<float>*>(smem + XTreeSmem<float>::off_tops(2 * nw));
+  float* xtop = reinterpret_cast<float*>(smem + XTreeSmem<float>::off_xtop(2 * nw));
+  Seg<float> S;
+  Node<float> ndc;
+  chunk_reduce_split<K, float>(d, s, S, ndc);
+  S = warp_tree_up<float>(S, nodes, lane, 5);  // every lane holds the warp's summary
+  cgx::cluster_group cl = cgx::this_cluster();
+  cluster_wait_started(2);
+  if (lane < 2) *cl.map_shared_rank(tops + rank * nw + warp, lane) = S;
+  cl.sync();
+  if (warp == 0) {
+    Eq<float> E0 = eq_identity<float>(), E1 = eq_identity<float>();
+    if (lane < 2 * nw) {
+      E0 = tops[lane].f;
+      E1 = tops[lane].l;
+    }
+    pcr64<float>(E0, E1, lane, 4 * nw);
+    if (lane < 2 * nw) {
+      xtop[2 * lane] = div_t(E0.d, E0.b);
+      xtop[2 * lane + 1] = div_t(E1.d, E1.b);
+    }
+  }
+  __syncthreads();
+  float xa = xtop[2 * (rank * nw + warp)];
+  float xc = xtop[2 * (rank * nw + warp) + 1];
+  warp_tree_down<float>(nodes, lane, 5, xa, xc);
+  chunk_backsub_split<K, float>(d, s, ndc, xa, xc);
+}
+
 }  // namespace adi

@@ -20,7 +20,8 @@ import math
 import numpy as np
 
 TUNING_KEYS = ("chunk_x", "chunk_y", "rows_per_cta", "cols_per_cta", "pcr_size", "use_graph",
-               "solver", "cta_threads", "cta_threads_y", "y_stage", "persist", "x_stage")
+               "solver", "cta_threads", "cta_threads_y", "y_stage", "persist", "x_stage",
+               "x_cluster")
 
 
 def main(argv=None):

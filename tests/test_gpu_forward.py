@@ -212,3 +212,18 @@ def test_staging_modes_match_oracle(nx, ny, xs, ys):
     o = oracle_run(m, phi, tau, steps, src=src, wavelet=wav)
     assert rel_l2(g["u_cur"], o["u_cur"]) < TOL
     assert rel_l2(g["u_prev"], o["u_prev"]) < TOL
+
+
+@pytest.mark.parametrize("nx,ny", [(16384, 9), (12000, 33), (9000, 20), (2500, 40)])
+@pytest.mark.parametrize("xc", [1, 2])
+def test_row_split_over_cta_pair_matches_oracle(nx, ny, xc):
+    """Rows solved by one CTA or split over a cluster of two (the halves
+    meet through DSMEM), including rows whose second half is mostly padding."""
+    steps = 4
+    m, phi, tau, src, wav = _problem(nx, ny, steps, seed=nx % 97 + ny)
+    tun = dict(x_stage=3, chunk_x=32, x_cluster=xc, rows_per_cta=1)
+    g = gpu_run(m, phi, tau, steps, src=src, wavelet=wav, tuning=tun)
+    assert g["tuning"]["x_cluster"] == xc
+    o = oracle_run(m, phi, tau, steps, src=src, wavelet=wav)
+    assert rel_l2(g["u_cur"], o["u_cur"]) < TOL
+    assert rel_l2(g["u_prev"], o["u_prev"]) < TOL
