@@ -55,10 +55,11 @@ BYTES_Y = 20  # read w, m, u^k, u^{k-1}; write u^{k+1}
 # dram__bytes_read.sum + dram__bytes_write.sum per 16384^2 launch, measured by
 # ncu on a smaller grid with the same launch shape and scaled by the number of
 # grid points: y_pipe_kernel on 4096 x 16384 (x 4,
-# profiles/y_pipe_kernel_4096x16384.txt), x_pipe_kernel on 16384 x 2048 (x 8,
-# profiles/x_pipe_kernel_16384x2048.txt).  Only valid for the 16384^2 workload.
+# profiles/y_pipe_kernel_4096x16384.txt), x_pipe_kernel (rows split over CTA
+# pairs) on 16384 x 2048 (x 8, profiles/x_pipe_kernel_16384x2048.txt).  Only
+# valid for the 16384^2 workload.
 NCU_TRAFFIC = {("ricker_16384", "y_pipe_kernel"): 5512502272,
-               ("ricker_16384", "x_pipe_kernel"): 2936647680}
+               ("ricker_16384", "x_pipe_kernel"): 2957748224}
 
 
 def measured_peak_gbs():
