@@ -77,15 +77,16 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
     if (K == 0) K = P.fp64x ? 8 : (G.nx >= 512 ? 16 : (G.nx >= 64 ? 8 : 4));
     // FP32 rows that fit 512 threads at 32 unknowns each: longer chunks win
     // (fewer interface equations per row, no register spills)
-    if (t.chunk_x == 0 && !P.fp64x && G.nx >= 1024 && next_pow2((G.nx + 31) / 32) <= std::min(maxT, 512)) K = 32;
+    // (from 2048 columns; at 1024 the adjoint's row solves run faster with K = 16)
+    if (t.chunk_x == 0 && !P.fp64x && G.nx >= 2048 && next_pow2((G.nx + 31) / 32) <= std::min(maxT, 512)) K = 32;
     if (K != 4 && K != 8 && K != 16 && K != 32) { why = "chunk_x must be 4, 8, 16 or 32"; return ADI_EINVAL; }
     while (next_pow2((G.nx + K - 1) / K) > maxT && K < 32) K *= 2;
     const int tsys = next_pow2((G.nx + K - 1) / K);
     if (tsys > maxT) { why = "nx too large for one CTA per row"; return ADI_EUNSUPPORTED; }
     int spc = t.rows_per_cta;
     // default: about 256 threads per CTA (one row per CTA once a row needs
-    // more), at least two CTAs per SM when the grid has the rows for it
-    if (spc == 0) spc = std::max(1, std::min(std::min(maxT, 256) / tsys, G.ny / 304));
+    // more), at least 256 CTAs when the grid has the rows for it
+    if (spc == 0) spc = std::max(1, std::min(std::min(maxT, 256) / tsys, G.ny / 256));
     if (spc < 1 || spc * tsys > maxT) { why = "rows_per_cta too large"; return ADI_EINVAL; }
     // whole warps only: the interface solve uses full-warp shuffles
     if (tsys < 32) {
