@@ -6,9 +6,12 @@
 //   pass 2, y_sweep_kernel: the column solves Y z = w, Y = I - S Lap_y
 //           (Eq. fr2's operator), fused with u^{k+1} = 2u^k - u^{k-1} + z,
 //           written over u^{k-1} (the buffer swap of Algorithm 1).
-// Both solve their lines with the cores of adi_sweeps.cuh.  Memory traffic
-// per grid point: pass 1 reads u^k and m and writes w (12 B, plus halo rows
-// served by L2); pass 2 reads w, m, u^k, u^{k-1} and writes u^{k+1} (20 B).
+// Both solve their lines with the cores of adi_sweeps.cuh.  Each pass also
+// exists as a TMA-pipelined persistent kernel (x_pipe_kernel, y_pipe_kernel:
+// the next tile streams into shared memory while the current one is
+// solved), the default for FP32 tree solves.  Memory traffic per grid point:
+// pass 1 reads u^k and m and writes w (12 B, plus halo rows served by L2);
+// pass 2 reads w, m, u^k, u^{k-1} and writes u^{k+1} (20 B).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
