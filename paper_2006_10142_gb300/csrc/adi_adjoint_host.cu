@@ -106,6 +106,16 @@ int adi_wave::adjoint(const float* resid, double* grad_m, float* grad_wavelet, i
   hg.n_wavelet = src_on ? rr.src.n_wavelet : 0;
 
   const GridPlan& P = G.plan;
+  // the column solves of the reverse step take the forward TMA pipeline
+  // when the forward y sweep does (strip maps of m and the three lam fields)
+  const bool ypipe = P.y_stage == 3 && !P.fp64y;
+  CUtensorMap tl_m, tl_L[3];
+  if (ypipe) {
+    const int BH = y_pipe_box_rows(1 << P.log2tcol, P.ky);
+    const int BW = 1 << P.log2W;
+    CKA(encode_strip_map(&tl_m, G.m, G.ld, G.ny, BW, BH), "strip map m");
+    for (int q = 0; q < 3; ++q) CKA(encode_strip_map(&tl_L[q], aw.L[q], G.ld, G.ny, BW, BH), "strip map lambda");
+  }
   float* L0 = aw.L[0];
   float* L1 = aw.L[1];
   float* L2 = aw.L[2];
@@ -134,12 +144,25 @@ int adi_wave::adjoint(const float* resid, double* grad_m, float* grad_wavelet, i
         CKA(launch_seed(L0, G.ld, aw.rec, n_rec, resid + (size_t)s * n_rec, st), "seed");
         launches += 1;
       }
-      YAdjArgs ya;
-      ya.nx = G.nx; ya.ny = G.ny; ya.ld = G.ld;
-      ya.log2W = P.log2W; ya.log2tcol = P.log2tcol; ya.C = P.C; ya.pcr = P.pcr;
-      ya.m = G.m; ya.lam = L0; ya.wbar = aw.wb;
-      ya.sc = G.dt * G.dt / (2.0 * G.hy * G.hy);
-      CKA(launch_y_adj(ya, P.ky, P.fp64y, st), "adjoint y sweep");
+      if (ypipe) {
+        YArgs ya = {};
+        ya.nx = G.nx; ya.ny = G.ny; ya.ld = G.ld;
+        ya.log2W = P.log2W; ya.log2tcol = P.log2tcol; ya.C = P.C; ya.pcr = P.pcr;
+        ya.m = G.m; ya.z_out = aw.wb;
+        ya.sc = G.dt * G.dt / (2.0 * G.hy * G.hy);
+        ya.err = d_err;
+        ya.stage_mode = 3;
+        ya.persist = 1;
+        const int q = L0 == aw.L[0] ? 0 : L0 == aw.L[1] ? 1 : 2;
+        CKA(launch_y_pipe_adj(ya, P.ky, tl_L[q], tl_m, st), "adjoint y sweep");
+      } else {
+        YAdjArgs ya;
+        ya.nx = G.nx; ya.ny = G.ny; ya.ld = G.ld;
+        ya.log2W = P.log2W; ya.log2tcol = P.log2tcol; ya.C = P.C; ya.pcr = P.pcr;
+        ya.m = G.m; ya.lam = L0; ya.wbar = aw.wb;
+        ya.sc = G.dt * G.dt / (2.0 * G.hy * G.hy);
+        CKA(launch_y_adj(ya, P.ky, P.fp64y, st), "adjoint y sweep");
+      }
       XAdjArgs xa;
       xa.nx = G.nx; xa.ny = G.ny; xa.ld = G.ld;
       xa.log2tsys = P.log2tsys; xa.spc = P.spc; xa.pcr = P.pcr;

@@ -324,8 +324,13 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT)) y_sweep_kernel(const YAr
 // [w tile] [m tile], each R x W floats, R = tcol * K rows of this CTA.
 // Rows beyond ny and columns beyond the row pitch arrive as zeros; columns
 // beyond nx are masked.
+// ADJ: the same pipeline solves the transposed column systems of the reverse
+// step, Y^T wbar = lam, through Y^T = S^{-1} Y S: the first tile is lam
+// (tm_w), the right-hand side is m . lam, and the epilogue writes
+// wbar = x / m to z_out (m read again from global memory); tm_uc and tm_up
+// are not used and nothing else is written.
 // ---------------------------------------------------------------------------
-template <int K, int MAXT, int W>
+template <int K, int MAXT, int W, bool ADJ>
 __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
     y_pipe_kernel(const YArgs a, const __grid_constant__ CUtensorMap tm_w,
                   const __grid_constant__ CUtensorMap tm_m, const __grid_constant__ CUtensorMap tm_uc,
@@ -360,8 +365,9 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
   const int lane = tid & 31;
   auto issue = [&](int st) {
     if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(2 * R * W * 4));
-    for (int t = lane; t < 4 * nbox; t += 32) {
-      const int b = t >> 2, f = t & 3;
+    constexpr int NF = ADJ ? 2 : 4;  // operations per box
+    for (int t = lane; t < NF * nbox; t += 32) {
+      const int b = t / NF, f = t % NF;
       const uint32_t off = (uint32_t)(b * BH * W * 4);
       if (f == 0) tma_load_2d(st_w + off, &tm_w, st * W, row0 + b * BH, bar);
       else if (f == 1) tma_load_2d(st_m + off, &tm_m, st * W, row0 + b * BH, bar);
@@ -373,8 +379,8 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
   if (tid < 32) {
     if (lane == 0) prefetch_tensormap(&tm_w);
     if (lane == 1) prefetch_tensormap(&tm_m);
-    if (lane == 2) prefetch_tensormap(&tm_uc);
-    if (lane == 3) prefetch_tensormap(&tm_up);
+    if (!ADJ && lane == 2) prefetch_tensormap(&tm_uc);
+    if (!ADJ && lane == 3) prefetch_tensormap(&tm_up);
     if (strip < nstrips) issue(strip);
   }
   const int col = tid & (W - 1);
@@ -422,7 +428,7 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
       }
 #pragma unroll
       for (int i = 0; i < QG; ++i) {
-        d[g + i] = colok ? vw[i] : 0.f;
+        d[g + i] = colok ? (ADJ ? vm[i] * vw[i] : vw[i]) : 0.f;
         s[g + i] = colok ? sc * vm[i] : 0.f;
       }
     }
@@ -435,7 +441,14 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
     // the cluster barrier at the top of the next strip keeps the owners'
     // shared memory alive until every remote read is done
     y_solve_cols<K, float, true>(smem, a.log2W, a.log2tcol, C, rank, a.pcr, col, gq, d, s, false);
-    if (colok) {
+    if (ADJ) {
+      if (colok) {
+        const size_t base = (size_t)j0 * ld + i;
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          if (j0 + k < a.ny) a.z_out[base + k * ld] = d[k] / __ldg(a.m + base + k * ld);
+      }
+    } else if (colok) {
       const size_t base = (size_t)j0 * ld + i;
       float chk = 0.f;
       if (j0 + K <= a.ny) {
@@ -473,7 +486,7 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
       }
       bad |= chk != 0.f;
     }
-    if (strip == 0 && rank == 0 && tid == 0 && a.gd) a.gd->k += 1;
+    if (!ADJ && strip == 0 && rank == 0 && tid == 0 && a.gd) a.gd->k += 1;
     __syncthreads();  // the solver's shared memory is reused by the next strip
   }
   if (C > 1) cgx::this_cluster().sync();  // no CTA leaves while its shared memory may be read
@@ -781,7 +794,7 @@ cudaError_t encode_strip_map(CUtensorMap* out, const float* base, int ld, int ny
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int K, int MAXT, int W>
+template <int K, int MAXT, int W, bool ADJ>
 static cudaError_t launch_y_pipe_t(const YArgs& a_in, const YMaps& mp, cudaStream_t st) {
   YArgs a = a_in;
   const int tcol = 1 << a.log2tcol;
@@ -804,21 +817,39 @@ static cudaError_t launch_y_pipe_t(const YArgs& a_in, const YMaps& mp, cudaStrea
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int nc = 0;
-  cudaError_t e = cudaOccupancyMaxActiveClusters(&nc, y_pipe_kernel<K, MAXT, W>, &cfg);
+  cudaError_t e = cudaOccupancyMaxActiveClusters(&nc, y_pipe_kernel<K, MAXT, W, ADJ>, &cfg);
   if (e != cudaSuccess) return e;
   cfg.gridDim = dim3(std::max(1, std::min(strips, nc)) * a.C, 1, 1);
-  return cudaLaunchKernelEx(&cfg, y_pipe_kernel<K, MAXT, W>, a, mp.w, mp.m, mp.uc, mp.up);
+  return cudaLaunchKernelEx(&cfg, y_pipe_kernel<K, MAXT, W, ADJ>, a, mp.w, mp.m, mp.uc, mp.up);
 }
 
 // 16-column strips (narrower strips, which fit smaller clusters, measured
 // far slower: their TMA boxes and row segments are 16 or 32 bytes wide).
-cudaError_t launch_y_pipe(const YArgs& a, int K, const YMaps& mp, cudaStream_t st) {
+template <bool ADJ>
+static cudaError_t launch_y_pipe_any(const YArgs& a, int K, const YMaps& mp, cudaStream_t st) {
   const int threads = 1 << (a.log2W + a.log2tcol);
   const int W = 1 << a.log2W;
   const bool small = threads <= 256;
-  if (K == 16 && W == 16) return small ? launch_y_pipe_t<16, 256, 16>(a, mp, st) : launch_y_pipe_t<16, 512, 16>(a, mp, st);
-  if (K == 32 && W == 16) return small ? launch_y_pipe_t<32, 256, 16>(a, mp, st) : launch_y_pipe_t<32, 512, 16>(a, mp, st);
+  if (K == 16 && W == 16)
+    return small ? launch_y_pipe_t<16, 256, 16, ADJ>(a, mp, st) : launch_y_pipe_t<16, 512, 16, ADJ>(a, mp, st);
+  if (K == 32 && W == 16)
+    return small ? launch_y_pipe_t<32, 256, 16, ADJ>(a, mp, st) : launch_y_pipe_t<32, 512, 16, ADJ>(a, mp, st);
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_y_pipe(const YArgs& a, int K, const YMaps& mp, cudaStream_t st) {
+  return launch_y_pipe_any<false>(a, K, mp, st);
+}
+
+cudaError_t launch_y_pipe_adj(const YArgs& a, int K, const CUtensorMap& lam, const CUtensorMap& m,
+                              cudaStream_t st) {
+  if (a.z_out == nullptr || a.m == nullptr) return cudaErrorInvalidValue;
+  YMaps mp;
+  mp.w = lam;
+  mp.m = m;
+  mp.uc = m;
+  mp.up = m;
+  return launch_y_pipe_any<true>(a, K, mp, st);
 }
 
 #define ADI_DISPATCH_K(FN, TT, MT, TR, ARGS)             \
@@ -902,10 +933,14 @@ cudaError_t configure_kernels() {
   ADI_CFG_SMALL(x_sweep_kernel, false, false)
   ADI_CFG_SMALL(y_sweep_kernel, true, true)
   ADI_CFG_SMALL(y_sweep_kernel, false, true)
-  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<16, 256, 16>, true);
-  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<16, 512, 16>, true);
-  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<32, 256, 16>, true);
-  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<32, 512, 16>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<16, 256, 16, false>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<16, 256, 16, true>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<16, 512, 16, false>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<16, 512, 16, true>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<32, 256, 16, false>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<32, 256, 16, true>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<32, 512, 16, false>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<32, 512, 16, true>, true);
   if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<8, 1024, 1>, false);
   if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<16, 256, 1>, false);
   if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<16, 512, 1>, false);

@@ -89,6 +89,10 @@ struct YMaps {
   CUtensorMap w, m, uc, up;
 };
 cudaError_t launch_y_pipe(const YArgs& a, int K, const YMaps& mp, cudaStream_t st);
+// The same kernel on the reverse step's column systems: wbar (z_out) from
+// lam (strip map `lam`) and m (a.m and strip map `m`); u fields unused.
+cudaError_t launch_y_pipe_adj(const YArgs& a, int K, const CUtensorMap& lam, const CUtensorMap& m,
+                              cudaStream_t st);
 // Row tensor map for the pipelined x sweep (see adi_tma.cuh).
 cudaError_t encode_row_map(CUtensorMap* out, const float* base, int ld, int ny, int box_lines);
 cudaError_t launch_x_pipe(const XArgs& a, int K, const CUtensorMap& tu, const CUtensorMap& tm,
