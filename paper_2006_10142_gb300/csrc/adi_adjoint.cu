@@ -17,12 +17,14 @@
 //   (tau^2/2) Lap_y z = (z - w)/m,  (tau^2/2) Lap_x w = (w - r)/m,
 //   tau^2 Lap u^k = (r - tau^2 f)/m,
 // so  dJ/dm += (wbar (z - w) + rbar (w - tau^2 f)) / m,
-// each step's increment formed in FP32 from the FP32 fields and accumulated
-// over the steps in FP64.
+// each step's increment formed in FP32 from the FP32 fields, summed in FP32
+// over the steps of one checkpoint segment and the segment sums accumulated
+// in FP64 (fold_grad_kernel).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "adi_adjoint.h"
+#include "adi_bodies.cuh"
 #include "adi_device.cuh"
 #include "adi_sweeps.cuh"
 
@@ -32,6 +34,9 @@ namespace adi {
 // 256 at 128 with two CTAs per SM (the launchers pick the smallest bound
 // that holds the CTA).
 constexpr int adj_min_ctas(int maxt) { return maxt <= 256 ? 2 : 1; }
+
+// Dynamic shared memory the adjoint kernels are configured for.
+constexpr size_t kAdjSmem = 200 * 1024;
 
 // Y^T wbar = lam (column solves): d = m . lam, solve with Y, wbar = x / m
 // (m is read again for the division rather than kept in registers).
@@ -76,7 +81,7 @@ __global__ void __launch_bounds__(MAXT, adj_min_ctas(MAXT)) y_adj_kernel(const Y
   if (colok) {
 #pragma unroll
     for (int k = 0; k < K; ++k)
-      if (j0 + k < a.ny) a.wbar[base + k * ld] = (float)(d[k] / (T)__ldg(a.m + base + k * ld));
+      if (j0 + k < a.ny) a.wbar[base + k * ld] = (float)(d[k] * (T)rcp_t(__ldg(a.m + base + k * ld)));
   }
 }
 
@@ -121,11 +126,16 @@ __global__ void __launch_bounds__(MAXT, adj_min_ctas(MAXT)) x_adj_kernel(const X
     load_vec<4>(wb, a.wbar + row + e);
     load_vec<4>(wf, a.w + row + e);
     load_vec<4>(zf, a.z + row + e);
+    float im[4], g[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) rb[k] = (e + k < a.nx) ? (float)(d[4 * c + k] / (T)mv[k]) : 0.f;
+    for (int k = 0; k < 4; ++k) {
+      im[k] = rcp_t(mv[k]);
+      rb[k] = (e + k < a.nx) ? (float)(d[4 * c + k] * (T)im[k]) : 0.f;
+    }
     store_vec<4, float>(a.rbar + row + e, rb);
-    // the step's increment is formed in FP32 (its inputs are FP32 fields);
-    // the running sum over all steps is FP64 (one FP64 add per node)
+    // the step's increment is formed in FP32 (its inputs are FP32 fields)
+    // and added to the segment's FP32 sum
+    load_vec<4>(g, a.g32 + row + e);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       if (e + k >= a.nx) continue;
@@ -134,12 +144,129 @@ __global__ void __launch_bounds__(MAXT, adj_min_ctas(MAXT)) x_adj_kernel(const X
       if (has_src && e + k == a.src_ix && a.wavelet != nullptr && a.level >= 0 &&
           a.level < a.n_wavelet)
         wsrc -= (float)(a.src_scale * (double)a.wavelet[a.level]);  // tau^2 f^k at the source
-      const float inc = (wb[k] * (zf[k] - wf[k]) + r_ * wsrc) / mv[k];
-      a.gm[(size_t)j * a.nx + e + k] += (double)inc;
+      g[k] += (wb[k] * (zf[k] - wf[k]) + r_ * wsrc) * im[k];
       if (has_src && e + k == a.src_ix && a.gw != nullptr && a.level >= 0 && a.level < a.n_wavelet)
         a.gw[a.level] += (float)(a.src_scale * (double)r_);
     }
+    store_vec<4, float>(a.g32 + row + e, g);
   }
+}
+
+// The same row solves and gradient terms with every global access coalesced
+// (FP32): m and wbar of the CTA's rows are read in float4 groups across the
+// CTA into shared memory (the 128-byte-swizzled order of swz4(), so the
+// coalesced writes and the per-thread chunk reads are both conflict-free);
+// after the solve each thread puts its chunk of x back, and the CTA forms
+// rbar = x / m and the gradient increment in float4 groups along the rows.
+// The arithmetic is that of x_adj_kernel, term for term.  Shared memory: [solver region] [x / m . wbar: spc x tsys K floats]
+// [s: same] at a.stage_off.
+template <int K, int MAXT>
+__global__ void __launch_bounds__(MAXT, adj_min_ctas(MAXT)) x_adj_staged_kernel(const XAdjArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int NQ = K / 4;  // float4 groups per thread
+  const int threads = blockDim.x;
+  const int tid = threadIdx.x;
+  const int log2row = a.log2tsys + (31 - __clz(K));  // elements per CTA row = tsys * K
+  const int rowlen = 1 << log2row;
+  float4* sd = reinterpret_cast<float4*>(smem + a.stage_off);
+  float4* ss = sd + threads * NQ;
+  const float sc = (float)a.sc;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int j0 = blockIdx.x * a.spc;
+
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int f = q * threads + tid;
+    const int e = f << 2;
+    const int col = e & (rowlen - 1);
+    const int j = j0 + (e >> log2row);
+    float4 m4 = z4, b4 = z4;
+    if (j < a.ny && col < a.nx) {
+      const size_t row = (size_t)j * a.ld;
+      m4 = __ldg(reinterpret_cast<const float4*>(a.m + row + col));
+      b4 = __ldg(reinterpret_cast<const float4*>(a.wbar + row + col));
+    }
+    const float mv[4] = {m4.x, m4.y, m4.z, m4.w};
+    const float wb[4] = {b4.x, b4.y, b4.z, b4.w};
+    float d[4], s[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const bool ok = j < a.ny && col + k < a.nx;
+      d[k] = ok ? mv[k] * wb[k] : 0.f;
+      s[k] = ok ? sc * mv[k] : 0.f;
+    }
+    sd[swz4(f)] = make_float4(d[0], d[1], d[2], d[3]);
+    ss[swz4(f)] = make_float4(s[0], s[1], s[2], s[3]);
+  }
+  __syncthreads();
+
+  float d[K], s[K];
+#pragma unroll
+  for (int c = 0; c < NQ; ++c) {
+    const float4 dv = sd[swz4(tid * NQ + c)];
+    const float4 sv = ss[swz4(tid * NQ + c)];
+    d[4 * c + 0] = dv.x; d[4 * c + 1] = dv.y; d[4 * c + 2] = dv.z; d[4 * c + 3] = dv.w;
+    s[4 * c + 0] = sv.x; s[4 * c + 1] = sv.y; s[4 * c + 2] = sv.z; s[4 * c + 3] = sv.w;
+  }
+  const int sys = tid >> a.log2tsys;
+  const int p = tid & ((1 << a.log2tsys) - 1);
+  x_solve_rows<K, float, true>(smem, a.spc, a.log2tsys, a.pcr, sys, p, d, s);
+#pragma unroll
+  for (int c = 0; c < NQ; ++c)
+    sd[swz4(tid * NQ + c)] = make_float4(d[4 * c + 0], d[4 * c + 1], d[4 * c + 2], d[4 * c + 3]);
+  __syncthreads();
+
+#pragma unroll 2
+  for (int q = 0; q < NQ; ++q) {
+    const int f = q * threads + tid;
+    const int e = f << 2;
+    const int col = e & (rowlen - 1);
+    const int j = j0 + (e >> log2row);
+    if (j >= a.ny || col >= a.nx) continue;
+    const size_t row = (size_t)j * a.ld;
+    const float4 x4 = sd[swz4(f)];
+    const float4 m4 = __ldg(reinterpret_cast<const float4*>(a.m + row + col));
+    const float4 b4 = __ldg(reinterpret_cast<const float4*>(a.wbar + row + col));
+    const float4 w4 = __ldcs(reinterpret_cast<const float4*>(a.w + row + col));
+    const float4 zz = __ldcs(reinterpret_cast<const float4*>(a.z + row + col));
+    const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
+    const float mv[4] = {m4.x, m4.y, m4.z, m4.w};
+    const float wb[4] = {b4.x, b4.y, b4.z, b4.w};
+    const float wf[4] = {w4.x, w4.y, w4.z, w4.w};
+    const float zf[4] = {zz.x, zz.y, zz.z, zz.w};
+    const bool has_src = j == a.src_iy && a.src_ix >= col && a.src_ix < col + 4;
+    float4* g4 = reinterpret_cast<float4*>(a.g32 + row + col);
+    const float4 gv = *g4;
+    float g[4] = {gv.x, gv.y, gv.z, gv.w};
+    float rb[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const bool ok = col + k < a.nx;
+      const float im = rcp_t(mv[k]);
+      rb[k] = ok ? xv[k] * im : 0.f;
+      float wsrc = wf[k];
+      if (has_src && col + k == a.src_ix && a.wavelet != nullptr && a.level >= 0 &&
+          a.level < a.n_wavelet)
+        wsrc -= (float)(a.src_scale * (double)a.wavelet[a.level]);  // tau^2 f^k at the source
+      if (ok) g[k] += (wb[k] * (zf[k] - wf[k]) + rb[k] * wsrc) * im;
+      if (ok && has_src && col + k == a.src_ix && a.gw != nullptr && a.level >= 0 &&
+          a.level < a.n_wavelet)
+        a.gw[a.level] += (float)(a.src_scale * (double)rb[k]);
+    }
+    *reinterpret_cast<float4*>(a.rbar + row + col) = make_float4(rb[0], rb[1], rb[2], rb[3]);
+    *g4 = make_float4(g[0], g[1], g[2], g[3]);
+  }
+}
+
+// gm += g32 (FP64), g32 = 0: the segment's FP32 sum joins the FP64 total.
+__global__ void fold_grad_kernel(double* __restrict__ gm, float* __restrict__ g32, int nx, int ny,
+                                 int ld) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= nx || j >= ny) return;
+  float* p = g32 + (size_t)j * ld + i;
+  gm[(size_t)j * nx + i] += (double)*p;
+  *p = 0.f;
 }
 
 // lam^k += 2 lam^{k+1} + tau^2 Lap(m . rbar);  lam^{k-1} -= lam^{k+1};  lam^{k+1} = 0.
@@ -186,12 +313,22 @@ __global__ void taylor_adj_kernel(TaylorArgs a) {
 
 // ---------------------------------------------------------------------------
 template <int K, typename T, int MAXT>
-static cudaError_t launch_xa_t(const XAdjArgs& a, cudaStream_t st) {
+static cudaError_t launch_xa_t(const XAdjArgs& a_in, cudaStream_t st) {
+  XAdjArgs a = a_in;
   const int threads = a.spc << a.log2tsys;
   if (threads % 32 != 0 || threads > MAXT) return cudaErrorInvalidValue;
   const int blocks = (a.ny + a.spc - 1) / a.spc;
-  const size_t sm = x_smem_bytes(a.spc, 1 << a.log2tsys, sizeof(T) == 8, true);
-  x_adj_kernel<K, T, MAXT><<<blocks, threads, sm, st>>>(a);
+  const size_t tree = x_smem_bytes(a.spc, 1 << a.log2tsys, sizeof(T) == 8, true);
+  if constexpr (sizeof(T) == 4) if (a.staged) {
+    // rows of tsys * K elements that hold the row (tsys K >= nx, from the planner)
+    const size_t sm = align64(tree) + x_stage_bytes(threads, K);
+    if (((size_t)K << a.log2tsys) >= (size_t)a.nx && sm <= kAdjSmem) {
+      a.stage_off = (int)align64(tree);
+      x_adj_staged_kernel<K, MAXT><<<blocks, threads, sm, st>>>(a);
+      return cudaGetLastError();
+    }
+  }
+  x_adj_kernel<K, T, MAXT><<<blocks, threads, tree, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -281,6 +418,12 @@ cudaError_t launch_seed(float* lam, int ld, const int* rec, int n_rec, const flo
   return cudaGetLastError();
 }
 
+cudaError_t launch_fold_grad(double* gm, float* g32, int nx, int ny, int ld, cudaStream_t st) {
+  dim3 block(256, 1, 1), grid((nx + 255) / 256, ny, 1);
+  fold_grad_kernel<<<grid, block, 0, st>>>(gm, g32, nx, ny, ld);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_taylor_adj(const TaylorArgs& a, cudaStream_t st) {
   dim3 block(256, 1, 1), grid((a.nx + 255) / 256, a.ny, 1);
   taylor_adj_kernel<<<grid, block, 0, st>>>(a);
@@ -289,7 +432,7 @@ cudaError_t launch_taylor_adj(const TaylorArgs& a, cudaStream_t st) {
 
 template <typename KernT>
 static cudaError_t allow_smem(KernT kern) {
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjSmem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   return e;
@@ -315,6 +458,14 @@ cudaError_t configure_adjoint_kernels() {
   ADI_CFG((y_adj_kernel<8, double, 512>))
   ADI_CFG((y_adj_kernel<16, double, 512>))
   ADI_CFG((y_adj_kernel<32, double, 512>))
+  ADI_CFG((x_adj_staged_kernel<4, 1024>))
+  ADI_CFG((x_adj_staged_kernel<8, 1024>))
+  ADI_CFG((x_adj_staged_kernel<16, 1024>))
+  ADI_CFG((x_adj_staged_kernel<32, 1024>))
+  ADI_CFG((x_adj_staged_kernel<16, 256>))
+  ADI_CFG((x_adj_staged_kernel<16, 512>))
+  ADI_CFG((x_adj_staged_kernel<32, 256>))
+  ADI_CFG((x_adj_staged_kernel<32, 512>))
   ADI_CFG((x_adj_kernel<16, float, 256>))
   ADI_CFG((x_adj_kernel<16, float, 512>))
   ADI_CFG((x_adj_kernel<32, float, 256>))

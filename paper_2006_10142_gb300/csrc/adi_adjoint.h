@@ -26,7 +26,7 @@ struct XAdjArgs {
   const float* w;    // forward x-sweep result of this step
   const float* z;    // forward y-sweep result of this step
   float* rbar;       // out
-  double* gm;        // [ny][nx] FP64, accumulated
+  float* g32;        // [ny][ld] FP32 sum of this checkpoint segment's dJ/dm increments
   float* gw;         // dJ/dwavelet or null
   long long level;   // k of this step
   double sc;         // tau^2 / (2 h1^2)
@@ -34,6 +34,8 @@ struct XAdjArgs {
   int src_ix, src_iy;
   const float* wavelet;
   int n_wavelet;
+  int staged;     // 1: FP32 rows staged through shared memory (coalesced), when it fits
+  int stage_off;  // set by the launcher
 };
 
 struct LamArgs {
@@ -63,6 +65,8 @@ cudaError_t launch_lam_update(const LamArgs& a, cudaStream_t st);
 cudaError_t launch_seed(float* lam, int ld, const int* rec, int n_rec, const float* resid,
                         cudaStream_t st);
 cudaError_t launch_taylor_adj(const TaylorArgs& a, cudaStream_t st);
+// gm[j][i] += g32[j][i] (FP64, [ny][nx]); g32 = 0 ([ny][ld]).
+cudaError_t launch_fold_grad(double* gm, float* g32, int nx, int ny, int ld, cudaStream_t st);
 cudaError_t configure_adjoint_kernels();
 
 }  // namespace adi

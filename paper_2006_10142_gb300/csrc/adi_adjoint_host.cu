@@ -6,7 +6,7 @@
 // checkpoint, recomputes the segment forward while storing the x-sweep result
 // w and the y-sweep result z of every step, then runs the reverse steps of
 // the segment backward (adi_adjoint.cu).  Memory: 2 fields per checkpoint +
-// 2 fields per step of one segment + 7 work fields.
+// 2 fields per step of one segment + 8 work fields.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,6 +29,7 @@ void adi_wave::free_adj_work() {
   cudaFree(aw.zseg);
   cudaFree(aw.wb);
   cudaFree(aw.rb);
+  cudaFree(aw.g32);
   for (int q = 0; q < 3; ++q) cudaFree(aw.L[q]);
   cudaFree(aw.A);
   cudaFree(aw.B);
@@ -45,6 +46,7 @@ int adi_wave::ensure_adj_work(Grid& G, int E, int n_rec) {
     if (e == cudaSuccess) e = cudaMalloc(&aw.zseg, fbytes * E);
     if (e == cudaSuccess) e = cudaMalloc(&aw.wb, fbytes);
     if (e == cudaSuccess) e = cudaMalloc(&aw.rb, fbytes);
+    if (e == cudaSuccess) e = cudaMalloc(&aw.g32, fbytes);
     for (int q = 0; q < 3 && e == cudaSuccess; ++q) e = cudaMalloc(&aw.L[q], fbytes);
     if (e == cudaSuccess) e = cudaMalloc(&aw.A, fbytes);
     if (e == cudaSuccess) e = cudaMalloc(&aw.B, fbytes);
@@ -95,6 +97,7 @@ int adi_wave::adjoint(const float* resid, double* grad_m, float* grad_wavelet, i
     CKA(cudaMemsetAsync(grad_wavelet, 0, sizeof(float) * (size_t)rr.src.n_wavelet, st),
         "clear grad_wavelet");
   for (int q = 0; q < 3; ++q) CKA(cudaMemsetAsync(aw.L[q], 0, fbytes, st), "clear lambda");
+  CKA(cudaMemsetAsync(aw.g32, 0, fbytes, st), "clear segment gradient");
   if (n_rec > 0)
     CKA(cudaMemcpyAsync(aw.rec, rr.rec.data(), sizeof(int) * 2 * (size_t)n_rec,
                         cudaMemcpyHostToDevice, st), "copy receivers");
@@ -116,6 +119,9 @@ int adi_wave::adjoint(const float* resid, double* grad_m, float* grad_wavelet, i
     CKA(encode_strip_map(&tl_m, G.m, G.ld, G.ny, BW, BH), "strip map m");
     for (int q = 0; q < 3; ++q) CKA(encode_strip_map(&tl_L[q], aw.L[q], G.ld, G.ny, BW, BH), "strip map lambda");
   }
+  // the row solves of the reverse step stage their rows through shared
+  // memory unless the forward x sweep is set to direct loads
+  const bool x_adj_staged = P.x_stage != 2;
   float* L0 = aw.L[0];
   float* L1 = aw.L[1];
   float* L2 = aw.L[2];
@@ -167,11 +173,12 @@ int adi_wave::adjoint(const float* resid, double* grad_m, float* grad_wavelet, i
       xa.nx = G.nx; xa.ny = G.ny; xa.ld = G.ld;
       xa.log2tsys = P.log2tsys; xa.spc = P.spc; xa.pcr = P.pcr;
       xa.m = G.m; xa.wbar = aw.wb; xa.w = aw.wseg + ffl * i; xa.z = aw.zseg + ffl * i;
-      xa.rbar = aw.rb; xa.gm = grad_m; xa.gw = grad_wavelet; xa.level = k;
+      xa.rbar = aw.rb; xa.g32 = aw.g32; xa.gw = grad_wavelet; xa.level = k;
       xa.sc = G.dt * G.dt / (2.0 * G.hx * G.hx);
       xa.src_scale = G.dt * G.dt / (G.hx * G.hy);
       xa.src_ix = hg.src_ix; xa.src_iy = hg.src_iy;
       xa.wavelet = hg.wavelet; xa.n_wavelet = hg.n_wavelet;
+      xa.staged = x_adj_staged ? 1 : 0; xa.stage_off = -1;
       CKA(launch_x_adj(xa, P.kx, P.fp64x, st), "adjoint x sweep");
       LamArgs la;
       la.nx = G.nx; la.ny = G.ny; la.ld = G.ld;
@@ -185,6 +192,9 @@ int adi_wave::adjoint(const float* resid, double* grad_m, float* grad_wavelet, i
       L1 = L2;
       L2 = t;
     }
+    // the segment's FP32 sum of dJ/dm increments joins the FP64 total
+    CKA(launch_fold_grad(grad_m, aw.g32, G.nx, G.ny, G.ld, st), "fold gradient");
+    launches += 1;
   }
   // L0 = dJ/du^{k0}; the second-order start makes u^1 depend on m and f^0
   if (rr.taylor) {

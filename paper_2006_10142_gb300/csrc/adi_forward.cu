@@ -327,7 +327,8 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT)) y_sweep_kernel(const YAr
 // ADJ: the same pipeline solves the transposed column systems of the reverse
 // step, Y^T wbar = lam, through Y^T = S^{-1} Y S: the first tile is lam
 // (tm_w), the right-hand side is m . lam, and the epilogue writes
-// wbar = x / m to z_out (m read again from global memory); tm_uc and tm_up
+// wbar = x / m to z_out (m read again from global memory, one approximate
+// reciprocal per node); tm_uc and tm_up
 // are not used and nothing else is written.
 // ---------------------------------------------------------------------------
 template <int K, int MAXT, int W, bool ADJ>
@@ -446,7 +447,7 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
         const size_t base = (size_t)j0 * ld + i;
 #pragma unroll
         for (int k = 0; k < K; ++k)
-          if (j0 + k < a.ny) a.z_out[base + k * ld] = d[k] / __ldg(a.m + base + k * ld);
+          if (j0 + k < a.ny) a.z_out[base + k * ld] = d[k] * rcp_t(__ldg(a.m + base + k * ld));
       }
     } else if (colok) {
       const size_t base = (size_t)j0 * ld + i;

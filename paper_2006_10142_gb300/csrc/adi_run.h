@@ -78,6 +78,7 @@ struct AdjWork {
   float* zseg = nullptr;  // [E] forward y-sweep results of a segment
   float* wb = nullptr;    // wbar
   float* rb = nullptr;    // rbar
+  float* g32 = nullptr;   // FP32 sum of dJ/dm increments over one segment
   float* L[3] = {nullptr, nullptr, nullptr};  // lam^{k+1}, lam^k, lam^{k-1}
   float* A = nullptr;     // recompute state
   float* B = nullptr;
