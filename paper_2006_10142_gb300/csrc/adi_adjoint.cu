@@ -269,22 +269,66 @@ __global__ void fold_grad_kernel(double* __restrict__ gm, float* __restrict__ g3
   *p = 0.f;
 }
 
-// lam^k += 2 lam^{k+1} + tau^2 Lap(m . rbar);  lam^{k-1} -= lam^{k+1};  lam^{k+1} = 0.
-__global__ void lam_update_kernel(LamArgs a) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// lam^k += 2 lam^{k+1} + tau^2 Lap(m . rbar) (+ the previous step's receiver
+// residuals);  lam^{k-1} -= lam^{k+1};  lam^{k+1} = 0.  Four nodes of a row
+// per thread (16-byte accesses; nodes past nx keep their values).
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+__global__ void __launch_bounds__(256) lam_update_kernel(LamArgs a) {
+  const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int j = blockIdx.y;
-  if (i >= a.nx || j >= a.ny) return;
-  const size_t c = (size_t)j * a.ld + i;
-  const float mr = __ldg(a.m + c) * __ldg(a.rbar + c);
-  const float l = (i > 0) ? __ldg(a.m + c - 1) * __ldg(a.rbar + c - 1) : 0.f;
-  const float r = (i + 1 < a.nx) ? __ldg(a.m + c + 1) * __ldg(a.rbar + c + 1) : 0.f;
-  const float dn = (j > 0) ? __ldg(a.m + c - a.ld) * __ldg(a.rbar + c - a.ld) : 0.f;
-  const float up = (j + 1 < a.ny) ? __ldg(a.m + c + a.ld) * __ldg(a.rbar + c + a.ld) : 0.f;
-  const float lap = a.cx * (l + r - 2.f * mr) + a.cy * (dn + up - 2.f * mr);
-  const float zb = a.L0[c];
-  a.L1[c] += 2.f * zb + lap;
-  a.L2[c] -= zb;
-  a.L0[c] = 0.f;
+  if (i0 >= a.nx || j >= a.ny) return;
+  const size_t c = (size_t)j * a.ld + i0;
+  // receiver range of this row first, so that its load overlaps the others
+  const int q0 = a.resid != nullptr ? __ldg(a.rrow + j) : 0;
+  const int q1 = a.resid != nullptr ? __ldg(a.rrow + j + 1) : 0;
+  auto prod = [&](size_t at) {
+    const float4 m4 = __ldg(reinterpret_cast<const float4*>(a.m + at));
+    const float4 r4 = __ldg(reinterpret_cast<const float4*>(a.rbar + at));
+    return make_float4(m4.x * r4.x, m4.y * r4.y, m4.z * r4.z, m4.w * r4.w);
+  };
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 p0 = prod(c);
+  const float4 pd = j > 0 ? prod(c - a.ld) : z4;
+  const float4 pu = j + 1 < a.ny ? prod(c + a.ld) : z4;
+  float mr[4] = {p0.x, p0.y, p0.z, p0.w};
+  const float dn[4] = {pd.x, pd.y, pd.z, pd.w};
+  const float up[4] = {pu.x, pu.y, pu.z, pu.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (i0 + k >= a.nx) mr[k] = 0.f;
+  const float mL = i0 > 0 ? __ldg(a.m + c - 1) * __ldg(a.rbar + c - 1) : 0.f;
+  const float mR = i0 + 4 < a.nx ? __ldg(a.m + c + 4) * __ldg(a.rbar + c + 4) : 0.f;
+  const float4 z0 = ld4(a.L0 + c), l1 = ld4(a.L1 + c), l2 = ld4(a.L2 + c);
+  const float zb[4] = {z0.x, z0.y, z0.z, z0.w};
+  float v1[4] = {l1.x, l1.y, l1.z, l1.w};
+  float v2[4] = {l2.x, l2.y, l2.z, l2.w};
+  float v0[4] = {z0.x, z0.y, z0.z, z0.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (i0 + k >= a.nx) continue;
+    const float l = k > 0 ? mr[k - 1] : mL;
+    const float r = k < 3 ? mr[k + 1] : mR;
+    const float lap = a.cx * (l + r - 2.f * mr[k]) + a.cy * (dn[k] + up[k] - 2.f * mr[k]);
+    v1[k] += 2.f * zb[k] + lap;
+    v2[k] -= zb[k];
+    v0[k] = 0.f;
+  }
+  for (int q = q0; q < q1; ++q) {
+    const int d = __ldg(a.rix + q) - i0;
+    if (d >= 0 && d < 4) {
+      const float rv = __ldg(a.resid + __ldg(a.rid + q));
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (k == d) v1[k] += rv;
+    }
+  }
+  st4(a.L1 + c, v1);
+  st4(a.L2 + c, v2);
+  st4(a.L0 + c, v0);
 }
 
 // lam[rec r] += resid[s][r] (receivers may share a node, hence the atomics).
@@ -406,7 +450,7 @@ cudaError_t launch_y_adj(const YAdjArgs& a, int K, bool fp64, cudaStream_t st) {
 }
 
 cudaError_t launch_lam_update(const LamArgs& a, cudaStream_t st) {
-  dim3 block(256, 1, 1), grid((a.nx + 255) / 256, a.ny, 1);
+  dim3 block(256, 1, 1), grid((a.nx + 1023) / 1024, a.ny, 1);
   lam_update_kernel<<<grid, block, 0, st>>>(a);
   return cudaGetLastError();
 }

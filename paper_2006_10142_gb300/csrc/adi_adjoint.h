@@ -46,6 +46,13 @@ struct LamArgs {
   float* L1;  // lam^k
   float* L2;  // lam^{k-1}
   float cx, cy;  // tau^2 / h1^2, tau^2 / h2^2
+  // receiver residuals of the previous step (u^k's misfit), added to lam^k
+  // at the receiver nodes, or null: the receivers of row j are
+  // rrow[j] .. rrow[j+1]-1, at columns rix[], residual index rid[]
+  const float* resid;
+  const int* rrow;
+  const int* rix;
+  const int* rid;
 };
 
 struct TaylorArgs {

@@ -59,16 +59,18 @@ int adi_wave::ensure_adj_work(Grid& G, int E, int n_rec) {
     aw.fbytes = fbytes;
     aw.E = E;
   }
-  if (n_rec > aw.rec_cap) {
+  // receivers [n_rec][2], then row offsets [ny + 1], columns [n_rec], indexes [n_rec]
+  const int rec_ints = 4 * n_rec + G.ny + 1;
+  if (rec_ints > aw.rec_cap) {
     cudaFree(aw.rec);
     aw.rec = nullptr;
     aw.rec_cap = 0;
-    cudaError_t e = cudaMalloc(&aw.rec, sizeof(int) * 2 * (size_t)n_rec);
+    cudaError_t e = cudaMalloc(&aw.rec, sizeof(int) * (size_t)rec_ints);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(this, ADI_ENOMEM, "allocate adjoint receivers");
     }
-    aw.rec_cap = n_rec;
+    aw.rec_cap = rec_ints;
   }
   return ADI_OK;
 }
@@ -98,9 +100,30 @@ int adi_wave::adjoint(const float* resid, double* grad_m, float* grad_wavelet, i
         "clear grad_wavelet");
   for (int q = 0; q < 3; ++q) CKA(cudaMemsetAsync(aw.L[q], 0, fbytes, st), "clear lambda");
   CKA(cudaMemsetAsync(aw.g32, 0, fbytes, st), "clear segment gradient");
-  if (n_rec > 0)
+  // Receivers grouped by row: the residual of step s - 1 is added to lam at
+  // the end of reverse step s (lam_update_kernel), that of the last step by
+  // one seed launch before the first.
+  int* d_rrow = aw.rec + 2 * n_rec;
+  int* d_rix = d_rrow + G.ny + 1;
+  int* d_rid = d_rix + n_rec;
+  if (n_rec > 0) {
+    std::vector<int>& t = aw.rtab;
+    t.assign((size_t)G.ny + 1 + 2 * (size_t)n_rec, 0);
+    for (int r = 0; r < n_rec; ++r) t[(size_t)rr.rec[2 * r + 1] + 1] += 1;
+    for (int j = 0; j < G.ny; ++j) t[(size_t)j + 1] += t[(size_t)j];
+    std::vector<int> fill(t.begin(), t.begin() + G.ny);
+    for (int r = 0; r < n_rec; ++r) {  // stable: receivers of a row keep their order
+      const int q = fill[rr.rec[2 * r + 1]]++;
+      t[(size_t)G.ny + 1 + q] = rr.rec[2 * r];
+      t[(size_t)G.ny + 1 + n_rec + q] = r;
+    }
     CKA(cudaMemcpyAsync(aw.rec, rr.rec.data(), sizeof(int) * 2 * (size_t)n_rec,
                         cudaMemcpyHostToDevice, st), "copy receivers");
+    CKA(cudaMemcpyAsync(d_rrow, t.data(), sizeof(int) * t.size(), cudaMemcpyHostToDevice, st),
+        "copy receiver table");
+    CKA(launch_seed(aw.L[0], G.ld, aw.rec, n_rec, resid + (size_t)(S - 1) * n_rec, st), "seed");
+    launches += 1;
+  }
 
   GridDev hg = {};
   hg.src_ix = src_on ? rr.src.ix : -1;
@@ -146,10 +169,6 @@ int adi_wave::adjoint(const float* resid, double* grad_m, float* grad_wavelet, i
     for (int i = len - 1; i >= 0; --i) {
       const int s = s0 + i;
       const long long k = rr.k0 + s;
-      if (n_rec > 0) {
-        CKA(launch_seed(L0, G.ld, aw.rec, n_rec, resid + (size_t)s * n_rec, st), "seed");
-        launches += 1;
-      }
       if (ypipe) {
         YArgs ya = {};
         ya.nx = G.nx; ya.ny = G.ny; ya.ld = G.ld;
@@ -185,6 +204,10 @@ int adi_wave::adjoint(const float* resid, double* grad_m, float* grad_wavelet, i
       la.m = G.m; la.rbar = aw.rb; la.L0 = L0; la.L1 = L1; la.L2 = L2;
       la.cx = (float)(G.dt * G.dt / (G.hx * G.hx));
       la.cy = (float)(G.dt * G.dt / (G.hy * G.hy));
+      la.resid = (n_rec > 0 && s > 0) ? resid + (size_t)(s - 1) * n_rec : nullptr;
+      la.rrow = d_rrow;
+      la.rix = d_rix;
+      la.rid = d_rid;
       CKA(launch_lam_update(la, st), "adjoint lambda update");
       launches += 3;
       float* t = L0;

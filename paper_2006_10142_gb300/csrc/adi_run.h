@@ -83,8 +83,9 @@ struct AdjWork {
   float* A = nullptr;     // recompute state
   float* B = nullptr;
   GridDev* gd = nullptr;
-  int* rec = nullptr;
-  int rec_cap = 0;
+  int* rec = nullptr;     // [n_rec][2] receivers, then the per-row table (see adjoint())
+  int rec_cap = 0;        // ints
+  std::vector<int> rtab;  // host copy of the per-row table
 };
 
 }  // namespace adi

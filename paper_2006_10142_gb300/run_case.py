@@ -10,6 +10,12 @@ square, or, with ``--medium const``, c = 1 (timing only: the kernels do the
 same work for any m).  ``--configs`` runs a list of tunings on the same
 inputs; every entry prints one JSON line.  Useful for profiling one kernel
 shape on a small device footprint and for tuning sweeps.
+
+  python -m paper_2006_10142_gb300.run_case --nx 1024 --ny 1024 --adjoint --steps 100
+
+``--adjoint`` records a run of ``--steps`` steps with 64 receivers along
+y = 0.1 and checkpoints every ``--every`` steps, then computes the gradient
+of the misfit against zero data once and reports its time per step.
 """
 from __future__ import annotations
 
@@ -32,6 +38,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--medium", choices=["seeded", "const"], default="seeded")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time one gradient (adjoint sweep) after a recorded run")
+    ap.add_argument("--every", type=int, default=50, help="checkpoint interval of --adjoint")
     ap.add_argument("--configs", type=str, default=None,
                     help="JSON list of tuning dicts to run one after the other")
     for k in TUNING_KEYS:
@@ -65,6 +74,9 @@ def main(argv=None):
         except api.AdiError as e:
             print(json.dumps({"nx": nx, "ny": ny, "config": cfg, "error": str(e)}))
             continue
+        if args.adjoint:
+            print(json.dumps(_adjoint_case(sim, args, src, wav, dev)), flush=True)
+            continue
         sim.run(args.warmup, src=src, wavelet=wav)
         sim.sync_status()
         sim.profile(True)
@@ -80,6 +92,26 @@ def main(argv=None):
         out["step_gbs_32B"] = 32 * pts / ((out["x_ms"] + out["y_ms"]) * 1e-3) / 1e9
         print(json.dumps(out), flush=True)
     sim.close()
+
+
+def _adjoint_case(sim, args, src, wav, dev):
+    import torch
+    from . import inputs
+    nx, ny = args.nx, args.ny
+    iy = inputs.nearest_node(0.1, ny)
+    rec = np.array([[min(nx - 1, int((r + 0.5) * nx / 64)), iy] for r in range(64)], dtype=np.int32)
+    sim.reset(torch.zeros((ny, nx), dtype=torch.float32, device=dev))
+    sim.set_checkpointing(args.every)
+    tr = sim.run(args.steps, src=src, wavelet=wav, rec=rec)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    gm, _ = sim.adjoint(tr, ckpt_every=args.every)
+    e1.record()
+    torch.cuda.synchronize()
+    sim.sync_status()
+    return {"nx": nx, "ny": ny, "steps": args.steps, "every": args.every, "tuning": sim.tuning(),
+            "adjoint_ms_per_step": e0.elapsed_time(e1) / args.steps,
+            "grad_m_finite": bool(torch.isfinite(gm).all().item())}
 
 
 if __name__ == "__main__":

@@ -79,7 +79,8 @@ def test_adjoint_matches_fp64_oracle(every):
 
 def _local_problem(n, steps, seed):
     """A problem whose gradient is not negligible after a few dozen steps:
-    16 receivers on a ring of radius 3-6 nodes around the source and a smooth
+    16 receivers on a ring of radius 3-6 nodes around the source (two of them
+    on one node) and a smooth
     seeded initial field u(0), so that lam (spreading from the receivers) and
     u overlap everywhere near the source from the first reverse step.
     tau = 2 h / max c (tau^2 m / h^2 <= 4, below the FP64 switch): the
@@ -94,6 +95,7 @@ def _local_problem(n, steps, seed):
     rad = 3 + (np.arange(16) % 4)
     rec = np.stack([np.clip(sx + np.round(rad * np.cos(ang)), 0, n - 1),
                     np.clip(sy + np.round(rad * np.sin(ang)), 0, n - 1)], axis=1)
+    rec[15] = rec[0]  # two receivers on one node: their residuals add
     prob.rec = rec.astype(np.int32)
     x = (np.arange(n) + 1.0) / (n + 1)
     phi = np.zeros((n, n))
