@@ -38,6 +38,10 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--medium", choices=["seeded", "const"], default="seeded")
+    ap.add_argument("--cfl", type=float, default=0.5,
+                    help="tau = cfl h / max c; above 3 the elimination switches to FP64")
+    ap.add_argument("--fp64", choices=["auto", "never", "always"], default="auto",
+                    help="FP64 elimination: when dominance is weak (auto), never, always")
     ap.add_argument("--adjoint", action="store_true",
                     help="time one gradient (adjoint sweep) after a recorded run")
     ap.add_argument("--every", type=int, default=50, help="checkpoint interval of --adjoint")
@@ -60,13 +64,13 @@ def main(argv=None):
         m_d = torch.from_numpy(m).to(dev)
         mmax = float(m.max())
     h = min(1.0 / (nx + 1), 1.0 / (ny + 1))
-    tau = 0.5 * h / math.sqrt(mmax)
+    tau = args.cfl * h / math.sqrt(mmax)
     configs = json.loads(args.configs) if args.configs else [
         {k: getattr(args, k) for k in TUNING_KEYS}]
     total = (args.warmup + args.steps) * len(configs)
     wav = torch.from_numpy(inputs.wavelet_samples(total + 2, tau).astype(np.float32)).to(dev)
     src = (inputs.nearest_node(0.5, nx), inputs.nearest_node(0.5, ny))
-    sim = api.AdiWave(m_d, torch.zeros_like(m_d), tau, src=src, wavelet=wav)
+    sim = api.AdiWave(m_d, torch.zeros_like(m_d), tau, src=src, wavelet=wav, fp64=args.fp64)
     pts = nx * ny
     for cfg in configs:
         try:
@@ -85,7 +89,9 @@ def main(argv=None):
         ms, cnt = sim.profile_read()
         sim.profile(False)
         sim.sync_status()
-        out = {"nx": nx, "ny": ny, "steps": args.steps, "config": cfg, "tuning": sim.tuning(),
+        out = {"nx": nx, "ny": ny, "steps": args.steps, "cfl": args.cfl, "fp64": args.fp64,
+               "config": cfg,
+               "tuning": sim.tuning(),
                "x_ms": ms[0] / max(cnt[0], 1), "y_ms": ms[1] / max(cnt[1], 1)}
         out["x_gbs"] = 12 * pts / (out["x_ms"] * 1e-3) / 1e9
         out["y_gbs"] = 20 * pts / (out["y_ms"] * 1e-3) / 1e9
