@@ -148,7 +148,9 @@ int adi_wave_set_checkpointing(adi_wave *h, int32_t every);
  * time; the forward fields are recomputed from checkpoints taken every
  * ckpt_every steps (reusing the run's checkpoints when they match).
  *   grad_m        device [ny][nx] FP64, overwritten with dJ/dm (m = c^2);
- *                 the accumulation over steps is done in FP64.
+ *                 each step's contribution is formed in FP32 and summed
+ *                 in FP32 over the steps of one checkpoint segment; the
+ *                 segment sums are accumulated in FP64.
  *   grad_wavelet  device [n_wavelet] FP32 dJ/dw(t_k), or NULL.
  * The handle's state (u^{k-1}, u^k) is left as it was after the run.
  * Returns ADI_ESTATE if no single-grid run was recorded. */

@@ -7,8 +7,8 @@ backward = adi_wave_adjoint.
 
 m is the coefficient of the Laplacian (c^2).  If m is built from a speed
 tensor c in torch (m = c * c), autograd applies dJ/dc = 2c dJ/dm itself.  The
-gradient wrt m is accumulated in FP64 by the library and returned in m's
-dtype (FP32).  Checkpoints of the forward run are kept every `ckpt_every`
+library sums the gradient wrt m in FP32 within a checkpoint segment and in
+FP64 across segments, and returns it in m's dtype (FP32).  Checkpoints of the forward run are kept every `ckpt_every`
 steps and the reverse sweep recomputes between them.
 """
 from __future__ import annotations
