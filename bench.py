@@ -58,7 +58,7 @@ BYTES_Y = 20  # read w, m, u^k, u^{k-1}; write u^{k+1}
 # profiles/y_pipe_kernel_4096x16384.txt), x_pipe_kernel (rows split over CTA
 # pairs) on 16384 x 2048 (x 8, profiles/x_pipe_kernel_16384x2048.txt).  Only
 # valid for the 16384^2 workload.
-NCU_TRAFFIC = {("ricker_16384", "y_pipe_kernel"): 5512502272,
+NCU_TRAFFIC = {("ricker_16384", "y_pipe_kernel"): 5692224512,
                ("ricker_16384", "x_pipe_kernel"): 2957748224}
 
 
