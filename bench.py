@@ -12,7 +12,8 @@ flush is needed between steps).
 Prints ONE JSON line (rank 0).  `value` is whole-job grid-point updates per
 second over the timed region (CUDA events on the launching stream, max over
 ranks); `e2e` is the same metric through the public API from pinned host
-buffers (H2D of m and phi, D2H of the final field inside the timed region);
+buffers (H2D of m and phi, D2H of the final field inside the timed region, on
+copy streams that overlap the neighbouring steps' compute);
 `roofline` reports the dominant kernel's algorithmic HBM bytes per launch over
 its average event-timed duration against the measured copy bandwidth;
 `cpu_baseline` is the FP64 oracle timed on the host cores on a bounded sample
@@ -358,29 +359,56 @@ def run_single(ctx):
         wav_h = (torch.from_numpy(prob.wavelet.astype(np.float32)).pin_memory()
                  if prob.wavelet is not None else None)
         out_h = torch.empty((n, n), dtype=torch.float32).pin_memory()
-        m_s = torch.empty_like(m_d)
-        phi_s = torch.empty_like(phi_d)
-        wav_s = torch.empty_like(wav_d) if wav_d is not None else None
+        # Each step uploads its inputs, runs and reads its result back.  The
+        # copies run on their own streams: the upload of step i + 1 (into the
+        # other of two device input sets) and the read-back of step i overlap
+        # the compute of the neighbouring steps.
+        comp = torch.cuda.current_stream()
+        up_st, down_st = torch.cuda.Stream(), torch.cuda.Stream()
+        sets = [(torch.empty_like(m_d), torch.empty_like(phi_d),
+                 torch.empty_like(wav_d) if wav_d is not None else None) for _ in range(2)]
+        uploaded = [torch.cuda.Event() for _ in range(2)]
+        consumed = [torch.cuda.Event() for _ in range(2)]
+        done = torch.cuda.Event()
 
-        def e2e_step():
-            m_s.copy_(m_h, non_blocking=True)
-            phi_s.copy_(phi_h, non_blocking=True)
-            if wav_s is not None:
-                wav_s.copy_(wav_h, non_blocking=True)
-            h.reset(phi_s, m=m_s)
-            h.run(ts, src=src, wavelet=wav_s)
-            _, uc, _ = h.state()
-            out_h.copy_(uc, non_blocking=True)
+        def upload(i):
+            m_s, phi_s, wav_s = sets[i % 2]
+            with torch.cuda.stream(up_st):
+                up_st.wait_event(consumed[i % 2])
+                m_s.copy_(m_h, non_blocking=True)
+                phi_s.copy_(phi_h, non_blocking=True)
+                if wav_s is not None:
+                    wav_s.copy_(wav_h, non_blocking=True)
+                uploaded[i % 2].record(up_st)
 
-        e2e_step()
-        torch.cuda.synchronize()
+        def e2e_steps(k):
+            for q in range(2):
+                consumed[q].record(comp)
+            upload(0)
+            for i in range(k):
+                m_s, phi_s, wav_s = sets[i % 2]
+                comp.wait_event(uploaded[i % 2])
+                h.reset(phi_s, m=m_s, stream=comp)
+                h.run(ts, src=src, wavelet=wav_s, stream=comp)
+                consumed[i % 2].record(comp)  # the run reads the wavelet until it ends
+                if i + 1 < k:
+                    upload(i + 1)
+                _, uc, _ = h.state(stream=comp)
+                done.record(comp)
+                with torch.cuda.stream(down_st):
+                    down_st.wait_event(done)
+                    out_h.copy_(uc, non_blocking=True)
+                uc.record_stream(down_st)
+            torch.cuda.synchronize()
+
+        e2e_steps(2)
         if world > 1:
             ctx["dist"].barrier()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            e2e_step()
-        torch.cuda.synchronize()
+        e2e_steps(args.steps)
         e_dt = _max_over_ranks(ctx, time.perf_counter() - t0)
+        if not torch.equal(out_h, h.state()[1].cpu()):
+            raise RuntimeError("e2e read-back differs from the final device state")
         bi = m_h.numel() * 4 + phi_h.numel() * 4 + (wav_h.numel() * 4 if wav_h is not None else 0)
         e2e = {"value": world * n * n * ts * args.steps / e_dt, "unit": UNIT,
                "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(n * n * 4)}
@@ -401,6 +429,8 @@ def run_single(ctx):
                        "source": "Ricker f=20" if wl["kind"] == "ricker" else "none",
                        "l2": "inputs larger than L2 (4 FP32 fields of %.0f MiB)" % (n * n * 4 / 2**20),
                        "timed_launches": "direct launches with per-kernel CUDA events",
+                       "e2e_copies": "per step: H2D of m, phi, wavelet and D2H of u on two copy "
+                                     "streams, overlapping the neighbouring steps' compute",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "tuning": h.tuning(), "autotuned": tuned is not None},
             "roofline": roof, "gpu_launches": int(launches), "clocks": clk, "e2e": e2e,

@@ -177,7 +177,8 @@ int adi_wave::start_grid(int s, const float* m, const float* phi, const float* p
       G.plan = old;
       return fail(this, rc, why);
     }
-    drop_graphs();
+    // the captured steps stay valid while the plan (launch shapes, kernels) is the same
+    if (!(G.plan == old)) drop_graphs();
   }
   G.hgd = GridDev{};
   G.hgd.k = 1;

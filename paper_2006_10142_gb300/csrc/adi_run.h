@@ -30,6 +30,14 @@ struct GridPlan {
   int persist = 0;   // 1: persistent sweeps with L2 prefetch of the next tile
   int x_stage = 2;   // 1: rows staged through shared memory, 2: direct, 3: TMA pipeline
   int xc = 1;        // TMA pipeline: CTAs per row (1 or 2)
+
+  bool operator==(const GridPlan& o) const {
+    return kx == o.kx && log2tsys == o.log2tsys && spc == o.spc && pcr == o.pcr &&
+           fp64x == o.fp64x && ky == o.ky && log2W == o.log2W && log2tcol == o.log2tcol &&
+           C == o.C && fp64y == o.fp64y && graph == o.graph && tree == o.tree &&
+           cta_threads == o.cta_threads && cta_threads_y == o.cta_threads_y &&
+           y_stage == o.y_stage && persist == o.persist && x_stage == o.x_stage && xc == o.xc;
+  }
 };
 
 struct Grid {

@@ -134,6 +134,36 @@ def test_fp64_fallback_weak_dominance(fp64):
     assert rel_l2(g["u_cur"], o["u_cur"]) < TOL
 
 
+@pytest.mark.parametrize("nx,ny,scale2", [(300, 260, 1.3), (1000, 700, 1.0), (120, 90, 60.0)])
+def test_reset_with_new_medium_matches_oracle(nx, ny, scale2):
+    """Run, then restart the same handle with another medium and initial field
+    (Eq. CN2 again) and run on: the captured step graphs are kept when the new
+    medium gives the same launch plan and rebuilt when it does not (scale 60
+    makes the systems weakly dominant, which switches to FP64 elimination)."""
+    import torch
+    from paper_2006_10142_gb300 import api
+    from helpers import f32
+    steps = 12
+    m1, phi1, tau, src, wav = _problem(nx, ny, steps, seed=5)
+    m2 = scale2 * inputs.m_field(nx, ny, 6)
+    phi2 = smooth_state(nx, ny, 7, 1e-2)
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.from_numpy(f32(a)).to(dev)
+    wav_t = t(wav)
+    h = api.AdiWave(t(m1), t(phi1), tau, src=src, wavelet=wav_t)
+    h.run(steps, src=src, wavelet=wav_t)
+    h.run(steps, src=src, wavelet=wav_t)  # graph replay on the first medium
+    h.reset(t(phi2), m=t(m2), src=src, wavelet=wav_t)
+    h.run(steps, src=src, wavelet=wav_t)
+    up, uc, k = h.state()
+    h.sync_status()
+    h.close()
+    assert k == steps + 1
+    o = oracle_run(m2, phi2, tau, steps, src=src, wavelet=wav)
+    assert rel_l2(uc.double().cpu().numpy(), o["u_cur"]) < TOL
+    assert rel_l2(up.double().cpu().numpy(), o["u_prev"]) < TOL
+
+
 def test_state_roundtrip_and_levels():
     import torch
     from paper_2006_10142_gb300 import api
