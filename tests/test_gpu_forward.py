@@ -121,15 +121,18 @@ def test_non_unit_domain():
     assert rel_l2(g["u_cur"], o["u_cur"]) < TOL
 
 
+@pytest.mark.parametrize("nx,ny", [(120, 90), (600, 70)])
 @pytest.mark.parametrize("fp64", ["auto", "always"])
-def test_fp64_fallback_weak_dominance(fp64):
-    """tau = 5h: (|a| + |c|)/|b| = 2s/(1 + 2s) > 0.9, the FP64 elimination path."""
-    nx, ny, steps = 120, 90, 10
+def test_fp64_fallback_weak_dominance(fp64, nx, ny):
+    """tau = 5h: (|a| + |c|)/|b| = 2s/(1 + 2s) > 0.9, the FP64 elimination path
+    (rows of 120: K = 8; rows of 600: K = 16)."""
+    steps = 10
     h = 1.0 / (nx + 1)
     m = np.ones((ny, nx))
     phi = smooth_state(nx, ny, 1)
     tau = 5 * h
     g = gpu_run(m, phi, tau, steps, fp64=fp64)
+    assert g["tuning"]["chunk_x"] == (16 if nx >= 512 else 8)
     o = oracle_run(m, phi, tau, steps)
     assert rel_l2(g["u_cur"], o["u_cur"]) < TOL
 
