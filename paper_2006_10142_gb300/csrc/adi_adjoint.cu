@@ -38,6 +38,20 @@ constexpr int adj_min_ctas(int maxt) { return maxt <= 256 ? 2 : 1; }
 // Dynamic shared memory the adjoint kernels are configured for.
 constexpr size_t kAdjSmem = 200 * 1024;
 
+// The source node's terms, in FP64 as before but out of line: only the
+// thread that holds the source node calls them, so no other warp issues
+// FP64 instructions (GB300 runs FP64 at 1/64 of the FP32 rate, and
+// predicated-off FP64 instructions in the element loops still took the
+// FP64 pipe's issue slots).
+// tau^2 f^k at the source node.
+__device__ __noinline__ float source_term(double src_scale, const float* wavelet, long long level) {
+  return (float)(src_scale * (double)wavelet[level]);
+}
+// dJ/dw(t_k) += tau^2 rbar_src / (h1 h2).
+__device__ __noinline__ void add_wavelet_grad(float* gw, long long level, double src_scale, float r) {
+  gw[level] += (float)(src_scale * (double)r);
+}
+
 // Y^T wbar = lam (column solves): d = m . lam, solve with Y, wbar = x / m
 // (m is read again for the division rather than kept in registers).
 template <int K, typename T, int MAXT>
@@ -118,6 +132,7 @@ __global__ void __launch_bounds__(MAXT, adj_min_ctas(MAXT)) x_adj_kernel(const X
   x_solve_rows<K, T, true>(smem, a.spc, a.log2tsys, a.pcr, sys, p, d, s);
   if (!active) return;
   const bool has_src = (j == a.src_iy) && a.src_ix >= i0 && a.src_ix < i0 + K;
+  const bool lev_ok = a.level >= 0 && a.level < a.n_wavelet;
 #pragma unroll
   for (int c = 0; c < K / 4; ++c) {
     const int e = i0 + 4 * c;
@@ -141,12 +156,11 @@ __global__ void __launch_bounds__(MAXT, adj_min_ctas(MAXT)) x_adj_kernel(const X
       if (e + k >= a.nx) continue;
       const float r_ = rb[k];
       float wsrc = wf[k];
-      if (has_src && e + k == a.src_ix && a.wavelet != nullptr && a.level >= 0 &&
-          a.level < a.n_wavelet)
-        wsrc -= (float)(a.src_scale * (double)a.wavelet[a.level]);  // tau^2 f^k at the source
+      if (has_src && e + k == a.src_ix) {
+        if (lev_ok && a.wavelet != nullptr) wsrc -= source_term(a.src_scale, a.wavelet, a.level);
+        if (lev_ok && a.gw != nullptr) add_wavelet_grad(a.gw, a.level, a.src_scale, r_);
+      }
       g[k] += (wb[k] * (zf[k] - wf[k]) + r_ * wsrc) * im[k];
-      if (has_src && e + k == a.src_ix && a.gw != nullptr && a.level >= 0 && a.level < a.n_wavelet)
-        a.gw[a.level] += (float)(a.src_scale * (double)r_);
     }
     store_vec<4, float>(a.g32 + row + e, g);
   }
@@ -235,6 +249,7 @@ __global__ void __launch_bounds__(MAXT, adj_min_ctas(MAXT)) x_adj_staged_kernel(
     const float wf[4] = {w4.x, w4.y, w4.z, w4.w};
     const float zf[4] = {zz.x, zz.y, zz.z, zz.w};
     const bool has_src = j == a.src_iy && a.src_ix >= col && a.src_ix < col + 4;
+    const bool lev_ok = a.level >= 0 && a.level < a.n_wavelet;
     float4* g4 = reinterpret_cast<float4*>(a.g32 + row + col);
     const float4 gv = *g4;
     float g[4] = {gv.x, gv.y, gv.z, gv.w};
@@ -245,13 +260,11 @@ __global__ void __launch_bounds__(MAXT, adj_min_ctas(MAXT)) x_adj_staged_kernel(
       const float im = rcp_t(mv[k]);
       rb[k] = ok ? xv[k] * im : 0.f;
       float wsrc = wf[k];
-      if (has_src && col + k == a.src_ix && a.wavelet != nullptr && a.level >= 0 &&
-          a.level < a.n_wavelet)
-        wsrc -= (float)(a.src_scale * (double)a.wavelet[a.level]);  // tau^2 f^k at the source
+      if (ok && has_src && col + k == a.src_ix) {
+        if (lev_ok && a.wavelet != nullptr) wsrc -= source_term(a.src_scale, a.wavelet, a.level);
+        if (lev_ok && a.gw != nullptr) add_wavelet_grad(a.gw, a.level, a.src_scale, rb[k]);
+      }
       if (ok) g[k] += (wb[k] * (zf[k] - wf[k]) + rb[k] * wsrc) * im;
-      if (ok && has_src && col + k == a.src_ix && a.gw != nullptr && a.level >= 0 &&
-          a.level < a.n_wavelet)
-        a.gw[a.level] += (float)(a.src_scale * (double)rb[k]);
     }
     *reinterpret_cast<float4*>(a.rbar + row + col) = make_float4(rb[0], rb[1], rb[2], rb[3]);
     *g4 = make_float4(g[0], g[1], g[2], g[3]);
