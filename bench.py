@@ -109,9 +109,15 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.thread.join(timeout=2)
+        return self.parse(self.lines)
+
+    @staticmethod
+    def parse(lines):
+        """Median SM clock, max clock and the throttle reasons seen in
+        `nvidia-smi --format=csv,noheader,nounits` lines of FIELDS."""
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 8:
                 continue
