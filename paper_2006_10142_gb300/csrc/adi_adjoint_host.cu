@@ -121,8 +121,10 @@ int adi_wave::adjoint(const float* resid, double* grad_m, float* grad_wavelet, i
                         cudaMemcpyHostToDevice, st), "copy receivers");
     CKA(cudaMemcpyAsync(d_rrow, t.data(), sizeof(int) * t.size(), cudaMemcpyHostToDevice, st),
         "copy receiver table");
-    CKA(launch_seed(aw.L[0], G.ld, aw.rec, n_rec, resid + (size_t)(S - 1) * n_rec, st), "seed");
-    launches += 1;
+    if (S > 0) {  // a recorded run has at least one step; the seed reads step S - 1
+      CKA(launch_seed(aw.L[0], G.ld, aw.rec, n_rec, resid + (size_t)(S - 1) * n_rec, st), "seed");
+      launches += 1;
+    }
   }
 
   GridDev hg = {};
