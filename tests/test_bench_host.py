@@ -25,9 +25,12 @@ def test_roofline_takes_the_kernel_with_the_most_time():
     assert r["achieved"] == pytest.approx(20 * n * n / 1.443e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert r["traffic"] == bench.NCU_TRAFFIC[("ricker_16384", "y_pipe_kernel")]
-    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-        peak = float(json.load(f)["hbm_gbs"])
-    assert r["peak"] == peak and r["peak_source"] == "measured"
+    peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")  # written per machine, not versioned
+    if os.path.exists(peaks):
+        with open(peaks) as f:
+            assert r["peak"] == float(json.load(f)["hbm_gbs"]) and r["peak_source"] == "measured"
+    else:
+        assert r["peak"] == 6800.0 and r["peak_source"] == "fallback"
     # another workload has no captured traffic
     assert bench._roofline(kms, kcnt, kinds, alg, "ricker_4096")["traffic"] is None
     # the x sweep dominates when it takes longer
