@@ -76,3 +76,33 @@ def test_null_handle_calls_are_rejected(lib):
     assert lib.adi_wave_adjoint(None, None, None, None, 0, None) == _lib.ADI_EINVAL
     assert lib.adi_wave_sync_status(None, None) == _lib.ADI_EINVAL
     lib.adi_wave_destroy(None)
+
+
+def test_step_noalloc_rejects_bad_arguments_without_gpu(lib):
+    """adi_wave_step_noalloc checks every argument before its first CUDA call;
+    the pointers here are never dereferenced (each call fails a check)."""
+    f = lib.adi_wave_step_noalloc
+    ok = _lib.Desc(100, 60, 1.0, 1.0, 0.001, 0, 0)
+    m, uc, up = 0x10000, 0x20000, 0x30000  # 16-byte aligned, distinct
+    EINVAL = _lib.ADI_EINVAL
+
+    def call(desc=ok, ld=128, m_max=1.0, m_=m, uc_=uc, up_=up, src=None, k=1):
+        return f(ctypes.byref(desc) if desc is not None else None, ld, m_max, m_, uc_, up_,
+                 src, k, None)
+
+    assert call(desc=None) == EINVAL
+    assert call(m_=None) == EINVAL and call(uc_=None) == EINVAL and call(up_=None) == EINVAL
+    assert call(desc=_lib.Desc(0, 60, 1.0, 1.0, 0.001, 0, 0)) == EINVAL       # nx < 1
+    assert call(desc=_lib.Desc(100, 60, 1.0, 1.0, 0.0, 0, 0)) == EINVAL       # dt <= 0
+    assert call(desc=_lib.Desc(100, 60, float("nan"), 1.0, 0.001, 0, 0)) == EINVAL
+    assert call(desc=_lib.Desc(100, 60, 1.0, 1.0, 0.001, 0, 7)) == EINVAL     # fp64 mode
+    assert call(ld=96) == EINVAL                                               # ld < nx
+    assert call(ld=130) == EINVAL                                              # not a multiple of 32
+    assert call(desc=_lib.Desc(4096, 2048, 1.0, 1.0, 0.001, 0, 0), ld=4096) == EINVAL  # > 2^22 floats
+    assert call(m_max=0.0) == EINVAL and call(m_max=float("inf")) == EINVAL
+    assert call(m_=m + 4) == EINVAL                                            # unaligned
+    assert call(up_=uc) == EINVAL                                              # aliasing
+    assert call(k=-1) == EINVAL
+    src = _lib.Source(100, 10, 0x40000, 5)                                     # ix outside
+    assert call(src=ctypes.byref(src)) == EINVAL
+    assert b"source" in lib.adi_wave_last_error(None)
