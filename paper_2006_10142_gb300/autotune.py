@@ -67,6 +67,45 @@ def candidates(nx: int, ny: int):
     return shared, xs, ys
 
 
+def search(measure, shared, xs, ys):
+    """(total ms, tuning, x_ms, y_ms) of the best setting, or None.
+
+    measure(cfg) returns (x_ms, y_ms) or None when the shape rejects cfg.
+    The planner's own choice (the empty tuning, all knobs automatic) is the
+    reference: a searched tuning replaces it only when it is faster.  For
+    each shared setting the x knobs are chosen by the x time with the y
+    sweep on automatic, then the y knobs by the y time with that x."""
+    ref = measure({})
+    best = (ref[0] + ref[1], {}, ref[0], ref[1]) if ref else None
+    for sh in shared:
+        bx = None
+        for xc in xs:
+            cfg = dict(sh)
+            cfg.update(xc)
+            r = measure(cfg)
+            if r and (bx is None or r[0] < bx[0]):
+                bx = (r[0], xc)
+        if bx is None:
+            continue
+        by = None
+        for yc in ys:
+            cfg = dict(sh)
+            cfg.update(bx[1])
+            cfg.update(yc)
+            r = measure(cfg)
+            if r and (by is None or r[1] < by[0]):
+                by = (r[1], yc)
+        if by is None:
+            continue
+        tot = bx[0] + by[0]
+        if best is None or tot < best[0]:
+            t = dict(sh)
+            t.update(bx[1])
+            t.update(by[1])
+            best = (tot, t, bx[0], by[0])
+    return best
+
+
 def tune(nx: int, ny: int, fp64: str = "auto", steps: int = 3, warmup: int = 1,
          use_cache: bool = True, verbose: bool = False) -> Dict:
     """Best tuning for an nx x ny grid: {'tuning': {...}, 'x_ms': .., 'y_ms': ..}."""
@@ -105,43 +144,12 @@ def tune(nx: int, ny: int, fp64: str = "auto", steps: int = 3, warmup: int = 1,
             print(json.dumps({"cfg": cfg, "x_ms": r[0], "y_ms": r[1]}))
         return r
 
-    # the planner's own choice (all knobs automatic) is the reference: a
-    # searched tuning replaces it only when it is faster
-    ref = measure({})
-    best = (ref[0] + ref[1], {}, ref[0], ref[1]) if ref else None
-    for sh in shared:
-        # x knobs with the y sweep on automatic, then y knobs with that x
-        bx = None
-        for xc in xs:
-            cfg = dict(sh)
-            cfg.update(xc)
-            r = measure(cfg)
-            if r and (bx is None or r[0] < bx[0]):
-                bx = (r[0], xc)
-        if bx is None:
-            continue
-        by = None
-        for yc in ys:
-            cfg = dict(sh)
-            cfg.update(bx[1])
-            cfg.update(yc)
-            r = measure(cfg)
-            if r and (by is None or r[1] < by[0]):
-                by = (r[1], yc)
-        if by is None:
-            continue
-        tot = bx[0] + by[0]
-        if best is None or tot < best[0]:
-            t = dict(sh)
-            t.update(bx[1])
-            t.update(by[1])
-            best = (tot, t, bx[0], by[0])
+    best = search(measure, shared, xs, ys)
     sim.sync_status()
     sim.close()
     if best is None:
         raise RuntimeError("no tuning candidate is valid for %dx%d" % (nx, ny))
-    tuning = best[1]
-    out = {"tuning": tuning, "x_ms": best[2], "y_ms": best[3]}
+    out = {"tuning": best[1], "x_ms": best[2], "y_ms": best[3]}
     if use_cache:
         cache = _load_cache()
         cache[key] = out
