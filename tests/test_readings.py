@@ -57,3 +57,34 @@ def test_literal_recurrence_iterated_matches_its_closed_form():
     literal, _, exact = _phases(n, cfl)
     # after `steps` full steps the literal scheme is far out of phase with the wave
     assert abs(math.cos(steps * literal) - math.cos(steps * exact)) > 0.5
+
+
+def test_listing1_coefficients_damp_every_mode():
+    """Reading C4: Listing 1's a = c = tau^2, b = 2 tau^2 + h^2,
+    f = h^2 u_old - 2 h^2 u^k, in the convention a y_{i-1} - b y_i + c y_{i+1} = f,
+    is the fully implicit (y - 2 u^k + u_old) / tau^2 = Lap_x y.  On one mode
+    its two roots have |r|^2 = 1 / (1 + tau^2 P) < 1 (every mode decays), while
+    the factored delta-form's roots lie on the unit circle (no damping)."""
+    n, cfl = 128, 1.0
+    h = 1.0 / (n + 1)
+    tau = cfl * h
+    P = 4.0 / h ** 2 * math.sin(math.pi * h / 2) ** 2
+    # the listing's row equation applied to the mode sin(pi x): y_{i-1} + y_{i+1} = (2 - h^2 P) y_i
+    a = c = tau * tau
+    b = 2 * tau * tau + h * h
+    lhs = a * (2 - h * h * P) - b            # coefficient of y_i after the neighbours
+    # lhs * y = h^2 (u_old - 2 u^k)  <=>  (1 + tau^2 P) y - 2 u^k + u_old = 0
+    assert -lhs / (h * h) == pytest.approx(1 + tau * tau * P, rel=1e-12)
+    r_listing = np.roots([1 + tau * tau * P, -2.0, 1.0])
+    assert np.allclose(np.abs(r_listing), (1 + tau * tau * P) ** -0.5)
+    assert (np.abs(r_listing) < 1).all()
+    S = tau * tau / 2
+    q = (1 + S * P) ** 2
+    r_factored = np.roots([q, -(2 * q - 2 * tau * tau * P), q])
+    assert np.allclose(np.abs(r_factored), 1.0)
+    # iterating the listing's recurrence: the amplitude decays as |r|^n
+    w = [1.0, 1.0]
+    for _ in range(200):
+        w.append((2 * w[-1] - w[-2]) / (1 + tau * tau * P))
+    env = (1 + tau * tau * P) ** -0.5
+    assert max(abs(x) for x in w[-20:]) < 2 * env ** 180
