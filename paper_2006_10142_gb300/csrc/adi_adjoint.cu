@@ -20,6 +20,10 @@
 // each step's increment formed in FP32 from the FP32 fields, summed in FP32
 // over the steps of one checkpoint segment and the segment sums accumulated
 // in FP64 (fold_grad_kernel).
+// The column solves run in y_pipe_kernel's adjoint mode (adi_forward.cu)
+// when the forward y sweep is pipelined, else in y_adj_kernel below; the
+// row solves in x_adj_staged_kernel (rows staged through shared memory) or
+// x_adj_kernel.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -38,11 +42,11 @@ constexpr int adj_min_ctas(int maxt) { return maxt <= 256 ? 2 : 1; }
 // Dynamic shared memory the adjoint kernels are configured for.
 constexpr size_t kAdjSmem = 200 * 1024;
 
-// The source node's terms, in FP64 as before but out of line: only the
-// thread that holds the source node calls them, so no other warp issues
-// FP64 instructions (GB300 runs FP64 at 1/64 of the FP32 rate, and
-// predicated-off FP64 instructions in the element loops still took the
-// FP64 pipe's issue slots).
+// The source node's terms, computed in FP64 out of line: only the thread
+// that holds the source node calls them, so no other warp issues FP64
+// instructions.  GB300 runs FP64 at 1/64 of the FP32 rate, and predicated
+// FP64 instructions inside the element loops would occupy the FP64 pipe in
+// every warp.
 // tau^2 f^k at the source node.
 __device__ __noinline__ float source_term(double src_scale, const float* wavelet, long long level) {
   return (float)(src_scale * (double)wavelet[level]);

@@ -5,7 +5,8 @@
 // visits the segments last to first; for each it restores the segment's
 // checkpoint, recomputes the segment forward while storing the x-sweep result
 // w and the y-sweep result z of every step, then runs the reverse steps of
-// the segment backward (adi_adjoint.cu).  Memory: 2 fields per checkpoint +
+// the segment backward (adi_adjoint.cu, and y_pipe_kernel's adjoint mode in
+// adi_forward.cu for the column solves).  Memory: 2 fields per checkpoint +
 // 2 fields per step of one segment + 8 work fields.
 #include <cuda_runtime.h>
 
