@@ -67,6 +67,7 @@ def _load():
                                            I, I, ci, D, ci]
             lib.oracle_adi_adjoint.argtypes = [ci, ci, cd, cd, cd, D, D, D, cl, ci, ci, ci, D, ci,
                                                I, I, ci, D, ci, D, D, D, D, ci]
+            lib.oracle_line_sweep.argtypes = [ci, ci, ci, ci, cd, cd, D, D, D, ci]
             lib.oracle_num_threads_available.argtypes = []
             _lib = lib
     return _lib
@@ -106,6 +107,20 @@ def thomas(a, b, c, d):
     if rc:
         raise RuntimeError("oracle_thomas failed (%d)" % rc)
     return x
+
+
+def line_sweep(m, rhs, h, tau, axis, transposed=False):
+    """Op^{-1} rhs for Op = X = I - S Lap_x (axis 1, along rows, h = h1) or
+    Y = I - S Lap_y (axis 0, along columns, h = h2), S = diag(tau^2 m / 2),
+    or for their transposes."""
+    m, rhs = _f64(m), _f64(rhs)
+    ny, nx = rhs.shape
+    out = np.empty_like(rhs)
+    rc = _load().oracle_line_sweep(0 if axis == 1 else 1, int(bool(transposed)), nx, ny,
+                                   float(h), float(tau), _dp(m), _dp(rhs), _dp(out), 1)
+    if rc:
+        raise RuntimeError("oracle_line_sweep failed (%d)" % rc)
+    return out
 
 
 def laplacian(u, hx, hy):

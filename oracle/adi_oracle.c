@@ -322,6 +322,19 @@ static int sweep_y_T(int nx, int ny, double hy, double tau, const double *m,
     return bad;
 }
 
+/* One sweep on its own (for tests of the operators): dir 0 solves along the
+ * rows (X, spacing h = h1), dir 1 along the columns (Y, h = h2); with
+ * transposed != 0 the transposed operator X^T or Y^T.  out = Op^{-1} rhs. */
+int oracle_line_sweep(int dir, int transposed, int nx, int ny, double h, double tau,
+                      const double *m, const double *rhs, double *out, int threads)
+{
+    if (dir == 0)
+        return transposed ? sweep_x_T(nx, ny, h, tau, m, rhs, out, threads)
+                          : sweep_x(nx, ny, h, tau, m, rhs, out, threads);
+    return transposed ? sweep_y_T(nx, ny, h, tau, m, rhs, out, threads)
+                      : sweep_y(nx, ny, h, tau, m, rhs, out, threads);
+}
+
 /* Reverse-mode derivative of J = 1/2 sum_s sum_r (traces[s][r] - d[s][r])^2
  * for the run oracle_adi_run(k0, steps, ...) would make from (u_prev0,
  * u_cur0).  resid[s*n_rec + r] = traces[s][r] - d[s][r] (= dJ/dtraces).

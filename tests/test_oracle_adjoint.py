@@ -85,3 +85,48 @@ def test_adjoint_state_gradients(oracle_mod):
     fd_p = (J(P["u_prev"] + eps * du, P["u_cur"]) - J(P["u_prev"] - eps * du, P["u_cur"])) / (2 * eps)
     assert abs(fd_c - np.sum(g["lam_cur"] * du)) <= 1e-6 * abs(fd_c)
     assert abs(fd_p - np.sum(g["lam_prev"] * du)) <= 1e-6 * abs(fd_p)
+
+
+def _dense_lap_1d(n, h):
+    """Second difference with the zero Dirichlet ring, as an n x n matrix."""
+    return (np.diag(-2.0 * np.ones(n)) + np.diag(np.ones(n - 1), 1)
+            + np.diag(np.ones(n - 1), -1)) / (h * h)
+
+
+@pytest.mark.parametrize("nx,ny", [(9, 7), (1, 5), (12, 1)])
+def test_single_sweeps_and_transposes_match_dense_solves(oracle_mod, nx, ny):
+    """X = I - S Lap_x and Y = I - S Lap_y (S = diag(tau^2 m / 2)) and their
+    transposes, built as dense matrices over the whole grid and solved by
+    numpy.linalg.solve, against the oracle's sweeps; then the dot-product
+    identity <Op^{-T} a, b> = <a, Op^{-1} b> for each operator."""
+    rng = np.random.default_rng(nx * 31 + ny)
+    hx, hy, tau = 1.0 / (nx + 1), 0.7 / (ny + 1), 0.03
+    m = 1.0 + 3.0 * rng.random((ny, nx))
+    S = np.diag(tau * tau * m.ravel() / 2.0)   # unknowns ordered j * nx + i
+    Lx = np.kron(np.eye(ny), _dense_lap_1d(nx, hx))
+    Ly = np.kron(_dense_lap_1d(ny, hy), np.eye(nx))
+    ops = {1: (np.eye(nx * ny) - S @ Lx, hx), 0: (np.eye(nx * ny) - S @ Ly, hy)}
+    a = rng.standard_normal((ny, nx))
+    b = rng.standard_normal((ny, nx))
+    for axis, (A, h) in ops.items():
+        fwd = oracle_mod.line_sweep(m, b, h, tau, axis)
+        tr = oracle_mod.line_sweep(m, a, h, tau, axis, transposed=True)
+        assert np.allclose(fwd.ravel(), np.linalg.solve(A, b.ravel()), rtol=1e-12, atol=1e-13)
+        assert np.allclose(tr.ravel(), np.linalg.solve(A.T, a.ravel()), rtol=1e-12, atol=1e-13)
+        lhs, rhs = np.vdot(tr, b), np.vdot(a, fwd)
+        assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + abs(rhs))
+
+
+def test_transposed_stencil_of_the_right_hand_side(oracle_mod):
+    """The reverse step takes tau^2 Lap(m . rbar) for the transpose of
+    u -> tau^2 m . Lap u: <m . Lap u, v> = <u, Lap(m . v)> (Lap symmetric with
+    the zero Dirichlet ring), on a non-square grid with h1 != h2."""
+    rng = np.random.default_rng(3)
+    ny, nx = 11, 16
+    hx, hy = 1.0 / (nx + 1), 1.3 / (ny + 1)
+    m = 1.0 + rng.random((ny, nx))
+    u = rng.standard_normal((ny, nx))
+    v = rng.standard_normal((ny, nx))
+    lhs = np.vdot(m * oracle_mod.laplacian(u, hx, hy), v)
+    rhs = np.vdot(u, oracle_mod.laplacian(m * v, hx, hy))
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + abs(rhs))
