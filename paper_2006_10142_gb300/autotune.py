@@ -20,9 +20,8 @@ from __future__ import annotations
 
 import itertools
 import json
-import math
 import os
-from typing import Dict, List, Optional
+from typing import Dict
 
 X_KNOBS = ("chunk_x", "rows_per_cta", "cta_threads", "x_stage")
 Y_KNOBS = ("chunk_y", "cols_per_cta", "cta_threads_y", "y_stage")
@@ -109,7 +108,6 @@ def search(measure, shared, xs, ys):
 def tune(nx: int, ny: int, fp64: str = "auto", steps: int = 3, warmup: int = 1,
          use_cache: bool = True, verbose: bool = False) -> Dict:
     """Best tuning for an nx x ny grid: {'tuning': {...}, 'x_ms': .., 'y_ms': ..}."""
-    import numpy as np
     import torch
 
     from . import api

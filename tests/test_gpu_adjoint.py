@@ -6,7 +6,6 @@ oracle adjoint on 64x64 grids (same FP32 inputs and residuals); at 1024x1024,
 2000 steps (checkpoint every 50), the directional derivative matches central
 differences of the GPU misfit within 1e-2 in 16 seeded directions.
 """
-import math
 
 import numpy as np
 import pytest

@@ -7,7 +7,6 @@ A whole FP64 run at these sizes is too slow for a test, so the checks are:
     oracle in FP64, against the GPU's next step (the step map itself);
   - sanity of the long run (finite, non-trivial, source energy arrived).
 """
-import math
 
 import numpy as np
 import pytest
