@@ -17,9 +17,10 @@
 //   (tau^2/2) Lap_y z = (z - w)/m,  (tau^2/2) Lap_x w = (w - r)/m,
 //   tau^2 Lap u^k = (r - tau^2 f)/m,
 // so  dJ/dm += (wbar (z - w) + rbar (w - tau^2 f)) / m,
-// each step's increment formed in FP32 from the FP32 fields, summed in FP32
-// over the steps of one checkpoint segment and the segment sums accumulated
-// in FP64 (fold_grad_kernel).
+// each step's increment formed in FP32 from the FP32 fields (z - w of two
+// FP32 values within a factor of two of each other is exact) and added to
+// an FP64 sum in the same pass: the reverse accumulation over all steps is
+// FP64.
 // The column solves run in y_pipe_kernel's adjoint mode (adi_forward.cu)
 // when the forward y sweep is pipelined, else in y_adj_kernel below; the
 // row solves in x_adj_staged_kernel (rows staged through shared memory) or
@@ -153,10 +154,12 @@ __global__ void __launch_bounds__(MAXT, adj_min_ctas(MAXT)) x_adj_kernel(const X
     }
     store_vec<4, float>(a.rbar + row + e, rb);
     // the step's increment is formed in FP32 (its inputs are FP32 fields)
-    // and added to the segment's FP32 sum
-    load_vec<4>(g, a.g32 + row + e);
+    // and added to the FP64 sum
+    double2* g2 = reinterpret_cast<double2*>(a.g64 + row + e);
+    double2 g01 = g2[0], g23 = g2[1];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
+      g[k] = 0.f;
       if (e + k >= a.nx) continue;
       const float r_ = rb[k];
       float wsrc = wf[k];
@@ -164,9 +167,12 @@ __global__ void __launch_bounds__(MAXT, adj_min_ctas(MAXT)) x_adj_kernel(const X
         if (lev_ok && a.wavelet != nullptr) wsrc -= source_term(a.src_scale, a.wavelet, a.level);
         if (lev_ok && a.gw != nullptr) add_wavelet_grad(a.gw, a.level, a.src_scale, r_);
       }
-      g[k] += (wb[k] * (zf[k] - wf[k]) + r_ * wsrc) * im[k];
+      g[k] = (wb[k] * (zf[k] - wf[k]) + r_ * wsrc) * im[k];
     }
-    store_vec<4, float>(a.g32 + row + e, g);
+    g01.x += (double)g[0]; g01.y += (double)g[1];
+    g23.x += (double)g[2]; g23.y += (double)g[3];
+    g2[0] = g01;
+    g2[1] = g23;
   }
 }
 
@@ -254,9 +260,11 @@ __global__ void __launch_bounds__(MAXT, adj_min_ctas(MAXT)) x_adj_staged_kernel(
     const float zf[4] = {zz.x, zz.y, zz.z, zz.w};
     const bool has_src = j == a.src_iy && a.src_ix >= col && a.src_ix < col + 4;
     const bool lev_ok = a.level >= 0 && a.level < a.n_wavelet;
-    float4* g4 = reinterpret_cast<float4*>(a.g32 + row + col);
-    const float4 gv = *g4;
-    float g[4] = {gv.x, gv.y, gv.z, gv.w};
+    // FP64 sum of the increments: two 16-byte groups per four nodes (the
+    // pitched rows of ld doubles keep them aligned)
+    double2* g2 = reinterpret_cast<double2*>(a.g64 + row + col);
+    double2 g01 = g2[0], g23 = g2[1];
+    float g[4] = {0.f, 0.f, 0.f, 0.f};
     float rb[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -268,22 +276,14 @@ __global__ void __launch_bounds__(MAXT, adj_min_ctas(MAXT)) x_adj_staged_kernel(
         if (lev_ok && a.wavelet != nullptr) wsrc -= source_term(a.src_scale, a.wavelet, a.level);
         if (lev_ok && a.gw != nullptr) add_wavelet_grad(a.gw, a.level, a.src_scale, rb[k]);
       }
-      if (ok) g[k] += (wb[k] * (zf[k] - wf[k]) + rb[k] * wsrc) * im;
+      if (ok) g[k] = (wb[k] * (zf[k] - wf[k]) + rb[k] * wsrc) * im;
     }
     *reinterpret_cast<float4*>(a.rbar + row + col) = make_float4(rb[0], rb[1], rb[2], rb[3]);
-    *g4 = make_float4(g[0], g[1], g[2], g[3]);
+    g01.x += (double)g[0]; g01.y += (double)g[1];
+    g23.x += (double)g[2]; g23.y += (double)g[3];
+    g2[0] = g01;
+    g2[1] = g23;
   }
-}
-
-// gm += g32 (FP64), g32 = 0: the segment's FP32 sum joins the FP64 total.
-__global__ void fold_grad_kernel(double* __restrict__ gm, float* __restrict__ g32, int nx, int ny,
-                                 int ld) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y;
-  if (i >= nx || j >= ny) return;
-  float* p = g32 + (size_t)j * ld + i;
-  gm[(size_t)j * nx + i] += (double)*p;
-  *p = 0.f;
 }
 
 // lam^k += 2 lam^{k+1} + tau^2 Lap(m . rbar) (+ the previous step's receiver
@@ -476,12 +476,6 @@ cudaError_t launch_seed(float* lam, int ld, const int* rec, int n_rec, const flo
                         cudaStream_t st) {
   if (n_rec <= 0) return cudaSuccess;
   seed_kernel<<<(n_rec + 127) / 128, 128, 0, st>>>(lam, ld, rec, n_rec, resid);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_fold_grad(double* gm, float* g32, int nx, int ny, int ld, cudaStream_t st) {
-  dim3 block(256, 1, 1), grid((nx + 255) / 256, ny, 1);
-  fold_grad_kernel<<<grid, block, 0, st>>>(gm, g32, nx, ny, ld);
   return cudaGetLastError();
 }
 

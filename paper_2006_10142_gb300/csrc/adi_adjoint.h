@@ -17,7 +17,7 @@ struct YAdjArgs {
   double sc;         // tau^2 / (2 h2^2)
 };
 
-// Row solves of X^T rbar = wbar + FP64 gradient accumulation.
+// Row solves of X^T rbar = wbar + the FP64 gradient accumulation.
 struct XAdjArgs {
   int nx, ny, ld;
   int log2tsys, spc, pcr;
@@ -26,7 +26,7 @@ struct XAdjArgs {
   const float* w;    // forward x-sweep result of this step
   const float* z;    // forward y-sweep result of this step
   float* rbar;       // out
-  float* g32;        // [ny][ld] FP32 sum of this checkpoint segment's dJ/dm increments
+  double* g64;       // [ny][ld] FP64 sum of the dJ/dm increments of every reverse step so far
   float* gw;         // dJ/dwavelet or null
   long long level;   // k of this step
   double sc;         // tau^2 / (2 h1^2)
@@ -72,8 +72,6 @@ cudaError_t launch_lam_update(const LamArgs& a, cudaStream_t st);
 cudaError_t launch_seed(float* lam, int ld, const int* rec, int n_rec, const float* resid,
                         cudaStream_t st);
 cudaError_t launch_taylor_adj(const TaylorArgs& a, cudaStream_t st);
-// gm[j][i] += g32[j][i] (FP64, [ny][nx]); g32 = 0 ([ny][ld]).
-cudaError_t launch_fold_grad(double* gm, float* g32, int nx, int ny, int ld, cudaStream_t st);
 cudaError_t configure_adjoint_kernels();
 
 }  // namespace adi
