@@ -148,9 +148,9 @@ int adi_wave_set_checkpointing(adi_wave *h, int32_t every);
  * time; the forward fields are recomputed from checkpoints taken every
  * ckpt_every steps (reusing the run's checkpoints when they match).
  *   grad_m        device [ny][nx] FP64, overwritten with dJ/dm (m = c^2);
- *                 each step's contribution is formed in FP32 and summed
- *                 in FP32 over the steps of one checkpoint segment; the
- *                 segment sums are accumulated in FP64.
+ *                 each reverse step's contribution is formed in FP32 from
+ *                 the FP32 fields and added to an FP64 sum (the reverse
+ *                 accumulation over all steps is FP64).
  *   grad_wavelet  device [n_wavelet] FP32 dJ/dw(t_k), or NULL.
  * The handle's state (u^{k-1}, u^k) is left as it was after the run.
  * Returns ADI_ESTATE if no single-grid run was recorded. */
@@ -159,12 +159,15 @@ int adi_wave_adjoint(adi_wave *h, const float *resid, double *grad_m,
 
 /* Copy the state of shot `shot` out: u_prev = u^{k-1}, u_cur = u^k (device
  * [ny][nx] each, either may be NULL) and *k = k (may be NULL; the level is
- * tracked on the host, so *k is exact when the call returns). */
+ * tracked on the host, so *k is exact when the call returns).  This is the
+ * state Algorithm 1 carries from one step to the next (its two time levels,
+ * u^k and the previous level U0, before the swap). */
 int adi_wave_get_state(const adi_wave *h, int32_t shot, float *u_prev,
                        float *u_cur, int64_t *k, void *stream);
 
-/* Replace the state of shot `shot` (device [ny][nx] each) and its level k.
- * Clears the recorded run. */
+/* Replace the state of shot `shot` (device [ny][nx] each) and its level k:
+ * Algorithm 1's two time levels (u^{k-1}, u^k) from which the next step
+ * starts.  Clears the recorded run. */
 int adi_wave_set_state(adi_wave *h, int32_t shot, const float *u_prev,
                        const float *u_cur, int64_t k, void *stream);
 
@@ -174,14 +177,18 @@ int adi_wave_set_state(adi_wave *h, int32_t shot, const float *u_prev,
 int adi_wave_sync_status(adi_wave *h, void *stream);
 
 /* Free everything the handle owns (device memory, graphs, events).  Waits
- * for the handle's outstanding work first.  NULL is ignored. */
+ * for the handle's outstanding work first.  NULL is ignored.  (Resource
+ * management of this library; the paper has no counterpart.) */
 void adi_wave_destroy(adi_wave *h);
 
-/* Static text for a return code. */
+/* Static text for a return code (error reporting of this library; the paper
+ * has no counterpart). */
 const char *adi_wave_strerror(int code);
 
 /* Detail of the last failing call on h (empty string if none); with h = NULL,
- * the detail of the last failed adi_wave_init on the calling thread. */
+ * the detail of the last failed adi_wave_init or adi_wave_step_noalloc on the
+ * calling thread.  The returned text is owned by the library and valid until
+ * the next call on h (or on the thread).  No counterpart in the paper. */
 const char *adi_wave_last_error(const adi_wave *h);
 
 /* ---- tuning (the autotuner's knobs) -------------------------------------
@@ -210,7 +217,14 @@ const char *adi_wave_last_error(const adi_wave *h);
  *                   (persistent clusters: the next strip's w and m arrive in
  *                   shared memory by bulk asynchronous copies while the
  *                   current strip is solved, and its u^k, u^{k-1} are
- *                   prefetched into L2; FP32 tree solver, 16 columns);
+ *                   prefetched into L2; FP32 tree solver, 16 columns) or
+ *                   ADI_STAGE_COOP (the same pipeline without clusters: a
+ *                   persistent grid of co-resident CTAs takes (strip,
+ *                   column segment) items and the segments of a column meet
+ *                   through global memory, so long columns do not need
+ *                   clusters of up to 16 CTAs; FP32 tree solver, 16
+ *                   columns, chunk_y 32 with 256 or 512 threads or
+ *                   chunk_y 16 with 512, at most 32 segments per column);
  * persist:          1 = one wave of resident CTAs (clusters) loops over the
  *                   tiles of each sweep and prefetches its next tile into L2
  *                   while solving the current one; -1 = one CTA per tile;
@@ -228,7 +242,7 @@ const char *adi_wave_last_error(const adi_wave *h);
  *                   CTA pair; two pairs fit an SM).
  * Zero fields mean "choose automatically". */
 enum { ADI_STAGE_AUTO = 0, ADI_STAGE_SMEM = 1, ADI_STAGE_L2 = 2, ADI_STAGE_DIRECT = 2,
-       ADI_STAGE_TMA = 3 };
+       ADI_STAGE_TMA = 3, ADI_STAGE_COOP = 4 /* y_stage only */ };
 enum { ADI_SOLVER_AUTO = 0, ADI_SOLVER_TREE = 1, ADI_SOLVER_CR_SMEM = 2 };
 typedef struct {
     int32_t chunk_x, chunk_y;
@@ -281,6 +295,52 @@ int adi_wave_set_wait_hook(adi_wave *h, int64_t spin_limit, int32_t never_ready_
  * kinds, graph replays counted per kernel node). */
 int64_t adi_wave_launch_count(const adi_wave *h);
 
+/* ---- problem class and scheme ----------------------------------------------
+ * Section 2 states the problem with a coefficient c(t) that depends on time
+ * (Eq. f1) and a general source f(t, x, y), and splits Eq. (CN1) into the two
+ * sub-problems of Eqs. (fr1) and (fr2) over half time levels; Listing 1 sets
+ * up the tridiagonal systems of a fully implicit form of them.  By default a
+ * handle solves the factored delta form of Eq. (CN1) with a time-independent
+ * coefficient m(x, y) and a point source (the form the benchmark workloads
+ * use).  adi_wave_set_model selects, for a single-grid handle:
+ *   ADI_SCHEME_FACTORED with g and/or f: Eq. (CN1) with the coefficient
+ *     m^k = g[k] m(x, y) at level k (levels past the end of g keep its last
+ *     value; g = NULL means 1) and a source field f^k (f = NULL means 0,
+ *     levels past n_f are 0) added to the point source.  CN1 weighs
+ *     Lap u^{k+1} by m^{k+1}/2 and Lap u^{k-1} by m^{k-1}/2, so a step solves
+ *     (I - S Lap) z = tau^2 (g_{k+1} m Lap u^k
+ *                            + (g_{k-1} - g_{k+1})/2 m Lap u^{k-1} + f^k),
+ *     S = tau^2 g_{k+1} m / 2, factored into an x and a y sweep as before.
+ *   ADI_SCHEME_HALF_LEVELS: Eqs. (fr1) and (fr2) as printed, over half time
+ *     levels: (I - S Lap_x) u^{k+1/2} = 2u^k - u^{k-1/2} + S Lap_x u^{k-1/2}
+ *     + tau^2 f^k, then (I - S Lap_y) u^{k+1} = 2u^{k+1/2} - u^k + S Lap_y u^k
+ *     + tau^2 f^{k+1/2}, S = tau^2 m / 2 (Algorithm 1's buffers u, U0, Ux,
+ *     Uy and its swaps).  The state reported by adi_wave_get_state is
+ *     (u^{k-1/2}, u^k); the start-up's (u^0, u^1) is taken as (u^{1/2}, u^1)
+ *     (with psi = 0 both equal phi, as Algorithm 1 starts).  This scheme
+ *     moves the waves too fast (by about sqrt 2).
+ *   ADI_SCHEME_LISTING1: the same half levels with Listing 1's systems
+ *     (a = c = tau^2 m, b = 2 tau^2 m + h^2, right-hand side from u^{k-1/2}
+ *     and u^k only): (I - tau^2 m Lap_x) u^{k+1/2} = 2u^k - u^{k-1/2}
+ *     + tau^2 f^k and the same along y; it damps every mode.
+ * The half-level schemes take no g or f (ADI_EINVAL); their point source at
+ * level k + 1/2 is the mean of the samples k and k + 1.  g and f are device
+ * arrays borrowed until the handle's last step that reads them; f is
+ * [n_f][ny][nx] FP32, contiguous.  With any non-default model the steps run
+ * as direct launches of one-shot kernels (no TMA pipeline, no graphs) with
+ * FP32 elimination, and adi_wave_adjoint returns ADI_EUNSUPPORTED.  Batched
+ * handles: ADI_EUNSUPPORTED.  Passing the default model restores the default
+ * path. */
+enum { ADI_SCHEME_FACTORED = 0, ADI_SCHEME_HALF_LEVELS = 1, ADI_SCHEME_LISTING1 = 2 };
+typedef struct {
+    int32_t scheme;   /* ADI_SCHEME_* */
+    const float *g;   /* device [n_g] or NULL */
+    int32_t n_g;
+    const float *f;   /* device [n_f][ny][nx] or NULL */
+    int32_t n_f;
+} adi_wave_model;
+int adi_wave_set_model(adi_wave *h, const adi_wave_model *model);
+
 /* ---- one step without allocation ------------------------------------------
  * The paper has no counterpart of this call: it is a library convenience.
  *
@@ -311,15 +371,18 @@ int64_t adi_wave_launch_count(const adi_wave *h);
  *   u_prev  device [ny][ld] u^{k-1} on entry, u^{k+1} on completion.
  *   src     host pointer to the point source or NULL; wavelet[k] is used.
  *   k       time level of u_cur (>= 0).
- * Buffers must be 16-byte aligned and u_cur != u_prev.  Non-finite values
- * are not reported by this call.
+ * Buffers must be 16-byte aligned and u_cur != u_prev.  This call reports
+ * no condition found on the GPU: non-finite values and an expired bounded
+ * wait inside the sweep kernels go unreported (the handle API reports both
+ * through adi_wave_sync_status).
  *
- * The first call on a device looks up the static array's address and sets
- * kernel attributes; make that first call before any stream capture that
- * should contain later calls.  The static array is shared by all calls on
- * a device: two calls whose work overlaps in time (different streams
- * without an event between them, or several host threads) race on it and
- * give wrong results.  Order them on one stream. */
+ * The first call on a device does a one-time set-up with that device
+ * current: it looks up the static array's address (cudaGetSymbolAddress)
+ * and sets kernel attributes.  Make that first call before any stream
+ * capture.  The static array is shared by all calls on a device and keeps
+ * the last call's contents: two calls whose work overlaps in time
+ * (different streams without an event between them, or several host
+ * threads) race on it and give wrong results.  Order them on one stream. */
 int adi_wave_step_noalloc(const adi_wave_desc *desc, int32_t ld, double m_max,
                           const float *m, const float *u_cur, float *u_prev,
                           const adi_source *src, int64_t k, void *stream);

@@ -42,7 +42,7 @@ EXPORTS = (
     "adi_wave_destroy", "adi_wave_strerror", "adi_wave_last_error", "adi_wave_get_tuning",
     "adi_wave_set_tuning", "adi_wave_profile", "adi_wave_profile_read", "adi_wave_launch_count",
     "adi_wave_version", "adi_wave_set_batch_mode", "adi_wave_set_wait_hook",
-    "adi_wave_step_noalloc",
+    "adi_wave_step_noalloc", "adi_wave_set_model",
 )
 
 
@@ -65,6 +65,11 @@ class Tuning(ctypes.Structure):
                 ("cta_threads_y", ctypes.c_int32), ("y_stage", ctypes.c_int32),
                 ("persist", ctypes.c_int32), ("x_stage", ctypes.c_int32),
                 ("x_cluster", ctypes.c_int32)]
+
+
+class Model(ctypes.Structure):
+    _fields_ = [("scheme", ctypes.c_int32), ("g", ctypes.c_void_p), ("n_g", ctypes.c_int32),
+                ("f", ctypes.c_void_p), ("n_f", ctypes.c_int32)]
 
 
 class AdiError(RuntimeError):
@@ -124,6 +129,7 @@ def load(build_if_missing: bool = True):
         lib.adi_wave_version.restype = ctypes.c_char_p
         lib.adi_wave_set_batch_mode.argtypes = [P, i32]
         lib.adi_wave_set_wait_hook.argtypes = [P, i64, i32]
+        lib.adi_wave_set_model.argtypes = [P, ctypes.POINTER(Model)]
         lib.adi_wave_step_noalloc.argtypes = [ctypes.POINTER(Desc), i32, ctypes.c_double, P, P, P,
                                               ctypes.POINTER(Source), i64, P]
         for name in EXPORTS:

@@ -140,6 +140,29 @@ class AdiWave:
         _lib.check(rc, self._h, "run")
         return traces
 
+    def set_model(self, scheme: str = "factored", g: Optional[torch.Tensor] = None,
+                  f: Optional[torch.Tensor] = None):
+        """adi_wave_set_model: scheme "factored" (Eq. CN1 in delta form; with g,
+        the coefficient m^k = g[k] m, and with f [n_f, ny, nx], a source field
+        f^k), "half_levels" (Eqs. fr1/fr2 as printed, over half time levels) or
+        "listing1" (Listing 1's systems over half levels).  g and f are kept
+        alive by the handle."""
+        schemes = {"factored": 0, "half_levels": 1, "listing1": 2}
+        if scheme not in schemes:
+            raise ValueError("scheme must be one of %s" % sorted(schemes))
+        if g is not None:
+            g = _dev_f32(g, "g")
+        if f is not None:
+            f = _dev_f32(f, "f")
+            if f.dim() != 3 or tuple(f.shape[1:]) != (self.ny, self.nx):
+                raise ValueError("f must be [n_f, %d, %d]" % (self.ny, self.nx))
+        mdl = _lib.Model(schemes[scheme], g.data_ptr() if g is not None else None,
+                         int(g.numel()) if g is not None else 0,
+                         f.data_ptr() if f is not None else None,
+                         int(f.shape[0]) if f is not None else 0)
+        _lib.check(self._lib.adi_wave_set_model(self._h, ctypes.byref(mdl)), self._h, "set_model")
+        self._model_keep = [g, f]
+
     def set_checkpointing(self, every: int):
         _lib.check(self._lib.adi_wave_set_checkpointing(self._h, int(every)), self._h)
 

@@ -58,11 +58,12 @@ def candidates(nx: int, ny: int):
     """(shared settings, x candidates, y candidates) for a grid shape."""
     shared = [dict(solver=1, pcr_size=0), dict(solver=2, pcr_size=8), dict(solver=2, pcr_size=32)]
     # stage 3 = the TMA-pipelined persistent sweeps, 2 = direct loads (x) or
-    # L2 prefetch (y), 1 = shared-memory staging
+    # L2 prefetch (y), 1 = shared-memory staging, 4 = (y only) persistent CTAs
+    # whose column segments meet through global memory
     xs = [dict(chunk_x=k, rows_per_cta=0, cta_threads=t, x_stage=s)
           for k, t, s in itertools.product((8, 16, 32), (256, 512, 1024), (3, 2))]
     ys = [dict(chunk_y=k, cols_per_cta=w, cta_threads_y=t, y_stage=s)
-          for k, w, t, s in itertools.product((8, 16, 32), (8, 16), (256, 512, 1024), (3, 1, 2))]
+          for k, w, t, s in itertools.product((8, 16, 32), (8, 16), (256, 512, 1024), (4, 3, 1, 2))]
     return shared, xs, ys
 
 

@@ -6,8 +6,10 @@
 // checkpoint, recomputes the segment forward while storing the x-sweep result
 // w and the y-sweep result z of every step, then runs the reverse steps of
 // the segment backward (adi_adjoint.cu, and y_pipe_kernel's adjoint mode in
-// adi_forward.cu for the column solves).  Memory: 2 fields per checkpoint +
-// 2 fields per step of one segment + 8 work fields.
+// adi_forward.cu for the column solves).  dJ/dm is summed in FP64 over all
+// reverse steps (a pitched [ny][ld] FP64 field) and copied to the caller's
+// array at the end.  Memory: 2 fields per checkpoint + 2 fields per step of
+// one segment + 7 FP32 work fields + the FP64 sum.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,7 +32,7 @@ void adi_wave::free_adj_work() {
   cudaFree(aw.zseg);
   cudaFree(aw.wb);
   cudaFree(aw.rb);
-  cudaFree(aw.g32);
+  cudaFree(aw.g64);
   for (int q = 0; q < 3; ++q) cudaFree(aw.L[q]);
   cudaFree(aw.A);
   cudaFree(aw.B);
@@ -47,7 +49,7 @@ int adi_wave::ensure_adj_work(Grid& G, int E, int n_rec) {
     if (e == cudaSuccess) e = cudaMalloc(&aw.zseg, fbytes * E);
     if (e == cudaSuccess) e = cudaMalloc(&aw.wb, fbytes);
     if (e == cudaSuccess) e = cudaMalloc(&aw.rb, fbytes);
-    if (e == cudaSuccess) e = cudaMalloc(&aw.g32, fbytes);
+    if (e == cudaSuccess) e = cudaMalloc(&aw.g64, 2 * fbytes);
     for (int q = 0; q < 3 && e == cudaSuccess; ++q) e = cudaMalloc(&aw.L[q], fbytes);
     if (e == cudaSuccess) e = cudaMalloc(&aw.A, fbytes);
     if (e == cudaSuccess) e = cudaMalloc(&aw.B, fbytes);
@@ -79,6 +81,7 @@ int adi_wave::ensure_adj_work(Grid& G, int E, int n_rec) {
 int adi_wave::adjoint(const float* resid, double* grad_m, float* grad_wavelet, int every,
                       cudaStream_t st) {
   if (g.size() != 1) return fail(this, ADI_EUNSUPPORTED, "adjoint of a batched handle");
+  if (model.active) return fail(this, ADI_EUNSUPPORTED, "adjoint of a non-default model");
   if (!rr.valid) return fail(this, ADI_ESTATE, "no recorded run to differentiate");
   if (rr.every <= 0)
     return fail(this, ADI_ESTATE,
@@ -94,13 +97,12 @@ int adi_wave::adjoint(const float* resid, double* grad_m, float* grad_wavelet, i
   const size_t fbytes = aw.fbytes;
   const size_t ffl = (size_t)G.ld * G.ny;  // floats per field
 
-  CKA(cudaMemsetAsync(grad_m, 0, sizeof(double) * (size_t)G.nx * G.ny, st), "clear grad_m");
   const bool src_on = rr.src.ix >= 0 && rr.src.wavelet != nullptr && rr.src.n_wavelet > 0;
   if (grad_wavelet && rr.src.n_wavelet > 0)
     CKA(cudaMemsetAsync(grad_wavelet, 0, sizeof(float) * (size_t)rr.src.n_wavelet, st),
         "clear grad_wavelet");
   for (int q = 0; q < 3; ++q) CKA(cudaMemsetAsync(aw.L[q], 0, fbytes, st), "clear lambda");
-  CKA(cudaMemsetAsync(aw.g32, 0, fbytes, st), "clear segment gradient");
+  CKA(cudaMemsetAsync(aw.g64, 0, 2 * fbytes, st), "clear gradient sum");
   // Receivers grouped by row: the residual of step s - 1 is added to lam at
   // the end of reverse step s (lam_update_kernel), that of the last step by
   // one seed launch before the first.
@@ -137,7 +139,7 @@ int adi_wave::adjoint(const float* resid, double* grad_m, float* grad_wavelet, i
   const GridPlan& P = G.plan;
   // the column solves of the reverse step take the forward TMA pipeline
   // when the forward y sweep does (strip maps of m and the three lam fields)
-  const bool ypipe = P.y_stage == 3 && !P.fp64y;
+  const bool ypipe = (P.y_stage == 3 || P.y_stage == 4) && !P.fp64y;
   CUtensorMap tl_m, tl_L[3];
   if (ypipe) {
     const int BH = y_pipe_box_rows(1 << P.log2tcol, P.ky);
@@ -182,7 +184,8 @@ int adi_wave::adjoint(const float* resid, double* grad_m, float* grad_wavelet, i
         ya.stage_mode = 3;
         ya.persist = 1;
         const int q = L0 == aw.L[0] ? 0 : L0 == aw.L[1] ? 1 : 2;
-        CKA(launch_y_pipe_adj(ya, P.ky, tl_L[q], tl_m, st), "adjoint y sweep");
+        if (P.y_stage == 4) CKA(launch_y_coop_adj(ya, P.ky, G.yc, tl_L[q], tl_m, st), "adjoint y sweep");
+        else CKA(launch_y_pipe_adj(ya, P.ky, tl_L[q], tl_m, st), "adjoint y sweep");
       } else {
         YAdjArgs ya;
         ya.nx = G.nx; ya.ny = G.ny; ya.ld = G.ld;
@@ -195,7 +198,7 @@ int adi_wave::adjoint(const float* resid, double* grad_m, float* grad_wavelet, i
       xa.nx = G.nx; xa.ny = G.ny; xa.ld = G.ld;
       xa.log2tsys = P.log2tsys; xa.spc = P.spc; xa.pcr = P.pcr;
       xa.m = G.m; xa.wbar = aw.wb; xa.w = aw.wseg + ffl * i; xa.z = aw.zseg + ffl * i;
-      xa.rbar = aw.rb; xa.g32 = aw.g32; xa.gw = grad_wavelet; xa.level = k;
+      xa.rbar = aw.rb; xa.g64 = aw.g64; xa.gw = grad_wavelet; xa.level = k;
       xa.sc = G.dt * G.dt / (2.0 * G.hx * G.hx);
       xa.src_scale = G.dt * G.dt / (G.hx * G.hy);
       xa.src_ix = hg.src_ix; xa.src_iy = hg.src_iy;
@@ -218,10 +221,11 @@ int adi_wave::adjoint(const float* resid, double* grad_m, float* grad_wavelet, i
       L1 = L2;
       L2 = t;
     }
-    // the segment's FP32 sum of dJ/dm increments joins the FP64 total
-    CKA(launch_fold_grad(grad_m, aw.g32, G.nx, G.ny, G.ld, st), "fold gradient");
-    launches += 1;
   }
+  // the FP64 sum (pitched rows) into the caller's [ny][nx] array
+  CKA(cudaMemcpy2DAsync(grad_m, sizeof(double) * (size_t)G.nx, aw.g64, sizeof(double) * (size_t)G.ld,
+                        sizeof(double) * (size_t)G.nx, G.ny, cudaMemcpyDeviceToDevice, st),
+      "copy gradient");
   // L0 = dJ/du^{k0}; the second-order start makes u^1 depend on m and f^0
   if (rr.taylor) {
     TaylorArgs ta;

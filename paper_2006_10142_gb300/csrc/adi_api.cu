@@ -184,12 +184,41 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
       }
     }
     if (K != 4 && K != 8 && K != 16 && K != 32) { why = "chunk_y must be 4, 8, 16 or 32"; return ADI_EINVAL; }
+    if (t.y_stage < ADI_STAGE_AUTO || t.y_stage > ADI_STAGE_COOP) { why = "unknown y_stage"; return ADI_EINVAL; }
     int tcol, C;
     geom(K, tcol, C);
+    // Column segments joined through global memory (adi_ycoop.cu): chosen on
+    // request, or automatically where the cluster form needs clusters of 8
+    // or more CTAs (which leave SMs idle) or cannot hold the column at all.
+    // 16 columns; K = 32 with 256 threads (512 for columns beyond 16384
+    // rows) or K = 16 with 512; at most 32 segments per column.
+    if (t.y_stage == ADI_STAGE_COOP || t.y_stage == ADI_STAGE_AUTO) {
+      const int cK = t.chunk_y ? t.chunk_y : 32;
+      const int cthr = cty ? cty : ((cK == 32 && (G.ny + 511) / 512 <= 32) ? 256 : 512);
+      const int ctc = cthr / 16;
+      const int cC = (G.ny + ctc * cK - 1) / (ctc * cK);
+      const bool shape_ok = (cK == 32 && (cthr == 256 || cthr == 512)) || (cK == 16 && cthr == 512);
+      const bool coop_ok = !P.fp64y && P.tree && (t.cols_per_cta == 0 || t.cols_per_cta == 16) &&
+                           shape_ok && cC >= 1 && cC <= 32 && ctc * cK >= 64 &&
+                           y_coop_smem_bytes(ctc, cK, cC) <= (size_t)kMaxDynSmem;
+      if (t.y_stage == ADI_STAGE_COOP && !coop_ok) {
+        why = "y segments through global memory not available for this shape";
+        return ADI_EUNSUPPORTED;
+      }
+      const bool want = t.y_stage == ADI_STAGE_COOP ||
+                        (coop_ok && W == 16 && t.chunk_y == 0 && cty == 0 && (!fits(K) || C >= 8));
+      if (want) {
+        P.y_stage = ADI_STAGE_COOP;
+        P.ky = cK;
+        P.log2W = 4;
+        P.log2tcol = ilog2(ctc);
+        P.C = cC;
+        goto y_done;
+      }
+    }
     if (!fits(K)) { why = "ny too large for this chunk_y (cluster or top system)"; return ADI_EUNSUPPORTED; }
     const size_t ysm = align64(y_smem_bytes(W, C, tcol, P.fp64y, P.tree));
     const size_t ystage = y_stage_bytes(W * tcol, K);
-    if (t.y_stage < ADI_STAGE_AUTO || t.y_stage > ADI_STAGE_TMA) { why = "unknown y_stage"; return ADI_EINVAL; }
     int stage = t.y_stage;
     // pipelined strips: FP32 tree solver, 16 columns, K >= 16, <= 512 threads
     const bool ypipe_ok = !P.fp64y && P.tree && W == 16 && (K == 32 || K == 16) &&
@@ -215,6 +244,7 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
     P.log2tcol = ilog2(tcol);
     P.C = C;
   }
+y_done:
   P.graph = (t.use_graph >= 0) ? 1 : 0;
   P.cta_threads = ct;
   P.cta_threads_y = cty;
@@ -388,6 +418,11 @@ extern "C" int adi_wave_set_batch_mode(adi_wave* h, int32_t mode) {
   h->batch_mode = mode;
   h->drop_graphs();
   return ADI_OK;
+}
+
+extern "C" int adi_wave_set_model(adi_wave* h, const adi_wave_model* model) {
+  if (!h || !model) return ADI_EINVAL;
+  return h->set_model(*model);
 }
 
 extern "C" int adi_wave_set_wait_hook(adi_wave* h, int64_t spin_limit, int32_t never_ready_shot) {

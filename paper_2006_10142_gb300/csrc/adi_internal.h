@@ -93,11 +93,68 @@ cudaError_t launch_y_pipe(const YArgs& a, int K, const YMaps& mp, cudaStream_t s
 // lam (strip map `lam`) and m (a.m and strip map `m`); u fields unused.
 cudaError_t launch_y_pipe_adj(const YArgs& a, int K, const CUtensorMap& lam, const CUtensorMap& m,
                               cudaStream_t st);
+// Column solves without clusters (adi_ycoop.cu): persistent co-resident CTAs
+// take (strip, segment) items; the C segments of a column meet through
+// global memory.  Scratch of one grid:
+struct YCoop {
+  int C;        // segments per column (1..32)
+  int strips;   // strips of 16 columns the scratch holds
+  float* tops;  // [strips][16][C] segment summaries, 8 floats each
+  int* sync;    // [strips][2] arrival / completion counters, zero between launches
+};
+size_t y_coop_smem_bytes(int tcol, int K, int C);
+int y_coop_segments(int ny, int tcol, int K);
+cudaError_t launch_y_coop(const YArgs& a, int K, const YCoop& yc, const YMaps& mp, cudaStream_t st);
+cudaError_t launch_y_coop_adj(const YArgs& a, int K, const YCoop& yc, const CUtensorMap& lam,
+                              const CUtensorMap& m, cudaStream_t st);
+cudaError_t configure_y_coop_kernels();
+
+// The wider problem class and the literal half-level schemes (adi_models.cu).
+// mode 0: Eq. CN1 with m^k = g_k m and a source field; 1: Eqs. fr1 / fr2 over
+// half levels; 2: Listing 1's systems over half levels.
+struct ModelXArgs {
+  int nx, ny, ld, log2tsys, spc, mode;
+  const float* m;
+  const float* a;     // mode 0: u^{k-1}; modes 1, 2: u^{k-1/2}
+  const float* b;     // u^k
+  float* out;         // mode 0: w; modes 1, 2: u^{k+1/2}
+  double cx, cy;      // tau^2 / h1^2, tau^2 / h2^2
+  double sc;          // tau^2 / (2 h1^2)
+  double src_scale;   // tau^2 / (h1 h2)
+  double tau2;        // tau^2
+  const float* g;     // [n_g] per-level factor of m (mode 0), or null
+  int n_g;
+  const float* f;     // [n_f][ny][nx] per-level source field (mode 0), or null
+  int n_f;
+  long long level;    // k
+  const GridDev* gd;  // point source
+};
+struct ModelYArgs {
+  int nx, ny, ld, log2W, log2tcol, C, mode;
+  const float* m;
+  const float* w;     // mode 0: the x pass's result; modes 1, 2: u^{k+1/2}
+  const float* b;     // u^k
+  float* io;          // mode 0: u^{k-1} in, u^{k+1} out; modes 1, 2: u^{k+1} out
+  double sc;          // tau^2 / (2 h2^2)
+  double src_scale;
+  const float* g;
+  int n_g;
+  long long level;
+  const GridDev* gd;
+  int* err;
+};
+cudaError_t launch_x_model(const ModelXArgs& a, int K, cudaStream_t st);
+cudaError_t launch_y_model(const ModelYArgs& a, int K, cudaStream_t st);
+cudaError_t launch_advance_level(GridDev* gd, cudaStream_t st);
+cudaError_t configure_model_kernels();
 // Row tensor map for the pipelined x sweep (see adi_tma.cuh).
 cudaError_t encode_row_map(CUtensorMap* out, const float* base, int ld, int ny, int box_lines);
 cudaError_t launch_x_pipe(const XArgs& a, int K, const CUtensorMap& tu, const CUtensorMap& tm,
                           const CUtensorMap& tw, cudaStream_t st);
 constexpr int kMaxDynSmem = 227 * 1024;
 cudaError_t configure_kernels();
+// Kernel attributes of every kernel of the library on the current device,
+// once per device (thread-safe); adi_run.cu.
+cudaError_t configure_current_device();
 
 }  // namespace adi

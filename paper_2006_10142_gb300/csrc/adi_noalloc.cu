@@ -6,8 +6,10 @@
 // kernels read.  Here both live in static device arrays of this translation
 // unit, sized at build time; their addresses are looked up once per device
 // with cudaGetSymbolAddress and handed to the same x / y sweep kernels the
-// handle API launches.  Nothing is allocated, on the device or through any
-// library, on any call.
+// handle API launches.  The record's values travel to the device as a kernel
+// argument (a one-thread kernel writes them into the static record), so no
+// host buffer is read after the call returns.  Nothing is allocated, on the
+// device or through any library, on any call.
 //
 // The static arrays are shared by every call on a device, so calls on one
 // device must not overlap: each must be ordered after the previous one has
@@ -57,7 +59,7 @@ int device_slot(DevSlot** out) {
   std::lock_guard<std::mutex> lock(g_mu);
   DevSlot& s = g_slots[dev];
   if (!s.ready) {
-    e = configure_kernels();
+    e = configure_current_device();
     if (e != cudaSuccess) return fail_msg(ADI_ECUDA, std::string("configure kernels: ") + cudaGetErrorString(e));
     void* w = nullptr;
     void* gd = nullptr;
@@ -74,6 +76,9 @@ int device_slot(DevSlot** out) {
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// The call's grid record, passed by value, into the static record.
+__global__ void set_record_kernel(GridDev hg, GridDev* dst) { *dst = hg; }
 
 }  // namespace
 
@@ -120,6 +125,9 @@ extern "C" int adi_wave_step_noalloc(const adi_wave_desc* desc, int32_t ld, doub
   rc = plan_grid(G, t, why);
   if (rc != ADI_OK) return fail_msg(rc, why);
   const GridPlan& P = G.plan;
+  // the y sweep without clusters needs scratch of its own; the default plan
+  // picks it only for grids far beyond the static array's limit
+  if (P.y_stage == ADI_STAGE_COOP) return fail_msg(ADI_EUNSUPPORTED, "grid shape needs the y sweep's own scratch");
 
   const cudaStream_t st = (cudaStream_t)stream;
   GridDev hg = {};
@@ -130,8 +138,9 @@ extern "C" int adi_wave_step_noalloc(const adi_wave_desc* desc, int32_t ld, doub
   hg.n_wavelet = on ? src->n_wavelet : 0;
   hg.src_ix = on ? src->ix : -1;
   hg.src_iy = on ? src->iy : -1;
-  cudaError_t e = cudaMemcpyAsync(slot->gd, &hg, sizeof(GridDev), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return fail_msg(ADI_ECUDA, std::string("upload grid record: ") + cudaGetErrorString(e));
+  set_record_kernel<<<1, 1, 0, st>>>(hg, slot->gd);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail_msg(ADI_ECUDA, std::string("grid record: ") + cudaGetErrorString(e));
 
   XArgs xa;
   xa.nx = d.nx;

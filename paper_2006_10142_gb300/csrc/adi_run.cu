@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -20,7 +21,11 @@ namespace {
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
-bool g_configured = false;
+// Kernel attributes (dynamic shared memory, cluster sizes) are per device:
+// one flag per device, set under a lock.
+constexpr int kMaxDevices = 64;
+bool g_configured[kMaxDevices] = {};
+std::mutex g_config_mu;
 
 #define CK(call, what)                                          \
   do {                                                          \
@@ -30,6 +35,50 @@ bool g_configured = false;
 
 }  // namespace
 
+cudaError_t adi::configure_current_device() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_config_mu);
+  if (g_configured[dev]) return cudaSuccess;
+  e = configure_kernels();
+  if (e == cudaSuccess) e = configure_adjoint_kernels();
+  if (e == cudaSuccess) e = configure_y_coop_kernels();
+  if (e == cudaSuccess) e = configure_model_kernels();
+  if (e == cudaSuccess) g_configured[dev] = true;
+  return e;
+}
+
+// Scratch of the y sweep without clusters (y_stage 4): segment summaries for
+// up to 32 segments per column and two counters per strip, zeroed once.
+int adi_wave::ensure_ycoop(Grid& G) {
+  if (G.plan.y_stage != ADI_STAGE_COOP) return ADI_OK;
+  const int strips = (G.nx + 15) / 16;
+  G.yc.C = G.plan.C;
+  if (G.yc.tops != nullptr && G.yc.strips >= strips) return ADI_OK;
+  cudaFree(G.yc.tops);
+  cudaFree(G.yc.sync);
+  G.yc.tops = nullptr;
+  G.yc.sync = nullptr;
+  G.yc.strips = 0;
+  cudaError_t e = cudaMalloc(&G.yc.tops, sizeof(float) * 8 * 16 * 32 * (size_t)strips);
+  if (e == cudaSuccess) e = cudaMalloc(&G.yc.sync, sizeof(int) * 2 * (size_t)strips);
+  if (e == cudaSuccess) e = cudaMemset(G.yc.sync, 0, sizeof(int) * 2 * (size_t)strips);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(G.yc.tops);
+    cudaFree(G.yc.sync);
+    G.yc.tops = nullptr;
+    G.yc.sync = nullptr;
+    return fail(this, e == cudaErrorMemoryAllocation ? ADI_ENOMEM : ADI_ECUDA,
+                std::string("y sweep scratch: ") + cudaGetErrorString(e));
+  }
+  G.yc.strips = strips;
+  return ADI_OK;
+}
+
 int adi_wave::upload_gd(Grid& G, cudaStream_t st) {
   CK(cudaMemcpyAsync(G.gd, &G.hgd, sizeof(GridDev), cudaMemcpyHostToDevice, st), "upload grid state");
   return ADI_OK;
@@ -38,11 +87,7 @@ int adi_wave::upload_gd(Grid& G, cudaStream_t st) {
 int adi_wave::create(const adi_wave_desc* desc, int n, const float* const* m,
                      const float* const* phi, const float* const* psi, const adi_source* src,
                      cudaStream_t st) {
-  if (!g_configured) {
-    CK(configure_kernels(), "configure kernels");
-    CK(configure_adjoint_kernels(), "configure adjoint kernels");
-    g_configured = true;
-  }
+  CK(configure_current_device(), "configure kernels");
   CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "create capture stream");
   CK(cudaMalloc(&d_err, sizeof(int)), "alloc error word");
   CK(cudaMemsetAsync(d_err, 0, sizeof(int), st), "clear error word");
@@ -179,6 +224,8 @@ int adi_wave::start_grid(int s, const float* m, const float* phi, const float* p
     }
     // the captured steps stay valid while the plan (launch shapes, kernels) is the same
     if (!(G.plan == old)) drop_graphs();
+    rc = ensure_ycoop(G);
+    if (rc != ADI_OK) return rc;
   }
   G.hgd = GridDev{};
   G.hgd.k = 1;
@@ -330,7 +377,7 @@ int adi_wave::launch_fwd(Grid& G, const float* u_cur, float* u_prev, float* w, f
   }
   if (profile && prof_end(st, a, ADI_KERNEL_X) != ADI_OK) return ADI_ECUDA;
   if (profile && prof_begin(st, &a) != ADI_OK) return ADI_ECUDA;
-  if (P.y_stage == 3) {
+  if (P.y_stage == 3 || P.y_stage == 4) {
     const int BH = y_pipe_box_rows(1 << P.log2tcol, P.ky);
     const int BW = 1 << P.log2W;
     if (G.ts_rows != BH * 64 + BW) {
@@ -351,7 +398,8 @@ int adi_wave::launch_fwd(Grid& G, const float* u_cur, float* u_prev, float* w, f
       else if (p == G.buf[1]) *outm[f] = G.ts_buf[1];
       else CK(encode_strip_map(outm[f], p, G.ld, G.ny, BW, BH), "strip map");
     }
-    CK(launch_y_pipe(ya, P.ky, mp, st), "y sweep launch");
+    if (P.y_stage == 4) CK(launch_y_coop(ya, P.ky, G.yc, mp, st), "y sweep launch");
+    else CK(launch_y_pipe(ya, P.ky, mp, st), "y sweep launch");
   } else {
     CK(launch_y(ya, P.ky, P.fp64y, P.tree, st), "y sweep launch");
   }
@@ -490,6 +538,13 @@ int adi_wave::run(int steps, const adi_source* src, const int32_t* rec_xy, int n
       seg = std::min(seg, every - s % every);
     }
     int t = 0;
+    if (model.active) {
+      while (t < seg) {
+        int rc = enqueue_model_step(G, st, gather);
+        if (rc != ADI_OK) return rc;
+        t += 1;
+      }
+    }
     if (use_graph) {
       while (seg - t >= 2) {
         int rc = launch_pair_graph(G, st, gather);
@@ -547,6 +602,13 @@ int adi_wave::set_tuning(const adi_wave_tuning& t) {
       return fail(this, rc, why);
     }
   }
+  for (auto& G : g) {
+    int rc = ensure_ycoop(G);
+    if (rc != ADI_OK) {
+      for (size_t s = 0; s < g.size(); ++s) g[s].plan = old[s];
+      return rc;
+    }
+  }
   tuning = t;
   drop_graphs();
   return ADI_OK;
@@ -581,6 +643,8 @@ adi_wave::~adi_wave() {
     cudaFree(G.buf[1]);
     cudaFree(G.w);
     cudaFree(G.gd);
+    cudaFree(G.yc.tops);
+    cudaFree(G.yc.sync);
   }
   for (float* p : rr.ckpt) cudaFree(p);
   free_adj_work();
@@ -598,3 +662,96 @@ adi_wave::~adi_wave() {
   if (cap) cudaStreamDestroy(cap);
 }
 
+
+// ---------------------------------------------------------------------------
+// problem class beyond the default (adi_models.cu)
+// ---------------------------------------------------------------------------
+int adi_wave::set_model(const adi_wave_model& mdl) {
+  if (g.size() != 1) return fail(this, ADI_EUNSUPPORTED, "models need a single-grid handle");
+  if (mdl.scheme < ADI_SCHEME_FACTORED || mdl.scheme > ADI_SCHEME_LISTING1)
+    return fail(this, ADI_EINVAL, "unknown scheme");
+  if (mdl.n_g < 0 || mdl.n_f < 0 || (mdl.g && mdl.n_g < 1) || (mdl.f && mdl.n_f < 1))
+    return fail(this, ADI_EINVAL, "bad g or f length");
+  if (mdl.scheme != ADI_SCHEME_FACTORED && (mdl.g || mdl.f))
+    return fail(this, ADI_EINVAL, "the half-level schemes take no g or f");
+  Model M;
+  M.scheme = mdl.scheme;
+  M.g = mdl.g;
+  M.n_g = mdl.g ? mdl.n_g : 0;
+  M.f = mdl.f;
+  M.n_f = mdl.f ? mdl.n_f : 0;
+  M.active = mdl.scheme != ADI_SCHEME_FACTORED || mdl.g != nullptr || mdl.f != nullptr;
+  if (M.active) {
+    // one-shot launch geometry: direct row loads, column strips over clusters
+    Grid tmp = g[0];
+    tmp.fp64mode = ADI_FP64_NEVER;
+    adi_wave_tuning t = tuning;
+    t.x_stage = ADI_STAGE_DIRECT;
+    t.y_stage = ADI_STAGE_L2;
+    t.solver = ADI_SOLVER_TREE;
+    t.x_cluster = 0;
+    std::string why;
+    int rc = plan_grid(tmp, t, why);
+    if (rc != ADI_OK) return fail(this, rc, "model launch geometry: " + why);
+    M.plan = tmp.plan;
+  }
+  model = M;
+  rr.valid = false;
+  drop_graphs();
+  return ADI_OK;
+}
+
+// One step of the active model: an x pass into the scratch field and a y pass,
+// then the level advances (and the receivers sample the new field).
+int adi_wave::enqueue_model_step(Grid& G, cudaStream_t st, bool gather) {
+  const GridPlan& P = model.plan;
+  float* A = G.buf[1 - G.cur];  // u^{k-1} (mode 0) or u^{k-1/2}
+  float* B = G.buf[G.cur];      // u^k
+  float* Wf = G.w;
+  const int mode = model.scheme;
+  ModelXArgs xa = {};
+  xa.nx = G.nx; xa.ny = G.ny; xa.ld = G.ld;
+  xa.log2tsys = P.log2tsys; xa.spc = P.spc; xa.mode = mode;
+  xa.m = G.m; xa.a = A; xa.b = B; xa.out = Wf;
+  xa.cx = G.dt * G.dt / (G.hx * G.hx);
+  xa.cy = G.dt * G.dt / (G.hy * G.hy);
+  xa.sc = G.dt * G.dt / (2.0 * G.hx * G.hx);
+  xa.src_scale = G.dt * G.dt / (G.hx * G.hy);
+  xa.tau2 = G.dt * G.dt;
+  xa.g = model.g; xa.n_g = model.n_g;
+  xa.f = model.f; xa.n_f = model.n_f;
+  xa.level = G.k;
+  xa.gd = G.gd;
+  ModelYArgs ya = {};
+  ya.nx = G.nx; ya.ny = G.ny; ya.ld = G.ld;
+  ya.log2W = P.log2W; ya.log2tcol = P.log2tcol; ya.C = P.C; ya.mode = mode;
+  ya.m = G.m; ya.w = Wf; ya.b = B; ya.io = A;
+  ya.sc = G.dt * G.dt / (2.0 * G.hy * G.hy);
+  ya.src_scale = G.dt * G.dt / (G.hx * G.hy);
+  ya.g = model.g; ya.n_g = model.n_g;
+  ya.level = G.k;
+  ya.gd = G.gd;
+  ya.err = d_err;
+  CK(launch_x_model(xa, P.kx, st), "model x pass");
+  CK(launch_y_model(ya, P.ky, st), "model y pass");
+  CK(launch_advance_level(G.gd, st), "advance level");
+  launches += 3;
+  if (gather) {
+    CK(launch_gather(G.gd, A, G.ld, G.hgd.n_rec, st), "gather launch");
+    launches += 1;
+  }
+  if (mode == ADI_SCHEME_FACTORED) {
+    G.cur = 1 - G.cur;  // u^{k+1} over u^{k-1}: the usual swap
+  } else {
+    // half levels: u^{k+1/2} is in the scratch field, u^{k+1} over u^{k-1/2},
+    // and u^k's buffer becomes the scratch (Algorithm 1's two swaps)
+    G.buf[1 - G.cur] = Wf;
+    G.buf[G.cur] = A;
+    G.w = B;
+    G.tm_lines = 0;  // cached tensor maps name the buffers by role
+    G.ts_rows = 0;
+  }
+  G.k += 1;
+  G.from_init = false;
+  return ADI_OK;
+}

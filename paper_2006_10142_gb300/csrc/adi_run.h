@@ -58,6 +58,7 @@ struct Grid {
   int tm_lines = 0;                 // box height they were encoded with, 0 = none
   CUtensorMap ts_buf[2], ts_m, ts_w;  // strip maps (pipelined y sweep)
   int ts_rows = 0;                  // 64 * box rows + box columns they were encoded with, 0 = none
+  YCoop yc = {0, 0, nullptr, nullptr};  // scratch of the y sweep without clusters (y_stage 4)
 };
 
 // What adi_wave_adjoint needs to replay the last run.
@@ -73,6 +74,18 @@ struct RunRecord {
   bool taylor = false;              // run started at level 1 right after a Taylor start-up
 };
 
+// Problem class of the handle (adi_wave_set_model); the default is the
+// factored delta form with a time-independent m and the point source only.
+struct Model {
+  int scheme = ADI_SCHEME_FACTORED;
+  const float* g = nullptr;
+  int n_g = 0;
+  const float* f = nullptr;
+  int n_f = 0;
+  bool active = false;  // anything but the default
+  GridPlan plan;        // one-shot launch geometry of the model kernels
+};
+
 struct ProfRec {
   cudaEvent_t a, b;
   int kind;
@@ -86,7 +99,7 @@ struct AdjWork {
   float* zseg = nullptr;  // [E] forward y-sweep results of a segment
   float* wb = nullptr;    // wbar
   float* rb = nullptr;    // rbar
-  float* g32 = nullptr;   // FP32 sum of dJ/dm increments over one segment
+  double* g64 = nullptr;  // [ny][ld] FP64 sum of the dJ/dm increments
   float* L[3] = {nullptr, nullptr, nullptr};  // lam^{k+1}, lam^k, lam^{k-1}
   float* A = nullptr;     // recompute state
   float* B = nullptr;
@@ -109,6 +122,7 @@ struct adi_wave {
   adi_wave_tuning tuning = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   int ckpt_every = 0;
   adi::RunRecord rr;
+  adi::Model model;
   adi::AdjWork aw;
   bool profile = false;
   std::vector<adi::ProfRec> prof;
@@ -158,6 +172,9 @@ struct adi_wave {
   int prof_begin(cudaStream_t st, cudaEvent_t* a);
   int prof_end(cudaStream_t st, cudaEvent_t a, int kind);
   int upload_gd(adi::Grid& G, cudaStream_t st);
+  int ensure_ycoop(adi::Grid& G);
+  int set_model(const adi_wave_model& m);
+  int enqueue_model_step(adi::Grid& G, cudaStream_t st, bool gather);
 };
 
 namespace adi {
