@@ -18,6 +18,13 @@ wrappers.  Each wrapper names the passage of the paper it follows:
                    scheme above (not in the paper; derived from it).
 - ``thomas``:      one tridiagonal solve (the serial method the paper's cyclic
                    reduction parallelises, Section 3.1).
+- ``adi_step_gen`` / ``adi_run_gen``: Eq. (CN1) with a time-dependent
+                   coefficient m^k = g_k m(x, y) (the c(t) of Eq. f1) and a
+                   source field f^k(x, y), in the same delta form and split.
+- ``adi_step_halves`` / ``adi_run_halves``: the sub-problems of Eqs. (fr1),
+                   (fr2) taken literally over half time levels (variant 1), and
+                   the fully implicit systems of Listing 1 (variant 2), with
+                   Algorithm 1's buffer rotation.
 """
 from __future__ import annotations
 
@@ -69,6 +76,10 @@ def _load():
                                                I, I, ci, D, ci, D, D, D, D, ci]
             lib.oracle_line_sweep.argtypes = [ci, ci, ci, ci, cd, cd, D, D, D, ci]
             lib.oracle_num_threads_available.argtypes = []
+            lib.oracle_adi_step_gen.argtypes = [ci, ci, cd, cd, cd, D, cd, cd, D, D, D, cd, ci, ci,
+                                                D, ci]
+            lib.oracle_adi_step_halves.argtypes = [ci, ci, ci, cd, cd, cd, D, D, D, cd, cd, ci, ci,
+                                                   D, D, ci]
             _lib = lib
     return _lib
 
@@ -219,3 +230,92 @@ def adi_adjoint(m, u_prev0, u_cur0, hx, hy, tau, steps, resid, rec, k0=1, src=No
     if rc:
         raise RuntimeError("oracle_adi_adjoint failed (%d)" % rc)
     return {"grad_m": gm, "grad_wavelet": gw, "lam_cur": lc, "lam_prev": lp}
+
+
+def _level(arr, k, hold_last):
+    """Sample k of a per-level array: beyond its end the last sample
+    (hold_last) or zero."""
+    if arr is None:
+        return None
+    if 0 <= k < len(arr):
+        return arr[k]
+    if hold_last and len(arr) > 0:
+        return arr[-1]
+    return None
+
+
+def adi_step_gen(m, u_prev, u_cur, hx, hy, tau, g_prev=1.0, g_next=1.0, fk=None, wv=0.0,
+                 src=None, threads=1):
+    """One step of Eq. (CN1) with m^k = g_k m and a source field f^k (CN1
+    weighs Lap u^{k+1} by m^{k+1}/2 and Lap u^{k-1} by m^{k-1}/2)."""
+    m, u_prev, u_cur, fk = _f64(m), _f64(u_prev), _f64(u_cur), _f64(fk)
+    ny, nx = u_cur.shape
+    out = np.empty_like(u_cur)
+    sx, sy = (-1, -1) if src is None else (int(src[0]), int(src[1]))
+    rc = _load().oracle_adi_step_gen(nx, ny, hx, hy, tau, _dp(m), float(g_prev), float(g_next),
+                                     _dp(u_prev), _dp(u_cur), _dp(fk), float(wv), sx, sy, _dp(out),
+                                     int(threads))
+    if rc:
+        raise RuntimeError("oracle_adi_step_gen failed (%d)" % rc)
+    return out
+
+
+def adi_run_gen(m, u_prev, u_cur, hx, hy, tau, steps, k0=1, g=None, f=None, src=None,
+                wavelet=None, rec=None, threads=1):
+    """`steps` steps of adi_step_gen from level k0.  g[k] scales m at level
+    k (levels past the end of g keep its last value; g = None is 1); f[k] is
+    the source field of level k (zero past its end); wavelet[k] the point
+    source.  Returns (u^{k0+steps-1}, u^{k0+steps}, traces)."""
+    up, uc = _f64(u_prev).copy(), _f64(u_cur).copy()
+    rec = None if rec is None else np.asarray(rec, dtype=np.int64).reshape(-1, 2)
+    tr = np.zeros((steps, 0 if rec is None else rec.shape[0]))
+    for s in range(steps):
+        k = k0 + s
+        gp = _level(g, k - 1, True)
+        gn = _level(g, k + 1, True)
+        fk = _level(f, k, False)
+        wv = _level(wavelet, k, False)
+        un = adi_step_gen(m, up, uc, hx, hy, tau, 1.0 if gp is None else gp,
+                          1.0 if gn is None else gn, fk, 0.0 if wv is None else wv, src, threads)
+        if rec is not None:
+            tr[s] = un[rec[:, 1], rec[:, 0]]
+        up, uc = uc, un
+    return up, uc, tr
+
+
+def adi_step_halves(variant, m, u_half_prev, u_cur, hx, hy, tau, wv_k=0.0, wv_half=0.0, src=None,
+                    threads=1):
+    """One step of the literal sub-schemes: (u^{k-1/2}, u^k) -> (u^{k+1/2},
+    u^{k+1}); variant 1 = Eqs. (fr1)/(fr2), variant 2 = Listing 1's systems."""
+    m, a, b = _f64(m), _f64(u_half_prev), _f64(u_cur)
+    ny, nx = b.shape
+    uh = np.empty_like(b)
+    un = np.empty_like(b)
+    sx, sy = (-1, -1) if src is None else (int(src[0]), int(src[1]))
+    rc = _load().oracle_adi_step_halves(int(variant), nx, ny, hx, hy, tau, _dp(m), _dp(a), _dp(b),
+                                        float(wv_k), float(wv_half), sx, sy, _dp(uh), _dp(un),
+                                        int(threads))
+    if rc:
+        raise RuntimeError("oracle_adi_step_halves failed (%d)" % rc)
+    return uh, un
+
+
+def adi_run_halves(variant, m, u_half_prev, u_cur, hx, hy, tau, steps, k0=1, src=None,
+                   wavelet=None, rec=None, threads=1):
+    """`steps` steps of adi_step_halves from level k0 (state (u^{k0-1/2},
+    u^{k0})).  The source at level k is wavelet[k]; at the half level k + 1/2
+    the mean of wavelet[k] and wavelet[k + 1] (zero past the end).  Returns
+    (u^{k0+steps-1/2}, u^{k0+steps}, traces of u^{k0+s+1})."""
+    a, b = _f64(u_half_prev).copy(), _f64(u_cur).copy()
+    rec = None if rec is None else np.asarray(rec, dtype=np.int64).reshape(-1, 2)
+    tr = np.zeros((steps, 0 if rec is None else rec.shape[0]))
+    for s in range(steps):
+        k = k0 + s
+        w0 = _level(wavelet, k, False)
+        w1 = _level(wavelet, k + 1, False)
+        w0 = 0.0 if w0 is None else float(w0)
+        w1 = 0.0 if w1 is None else float(w1)
+        a, b = adi_step_halves(variant, m, a, b, hx, hy, tau, w0, 0.5 * (w0 + w1), src, threads)
+        if rec is not None:
+            tr[s] = b[rec[:, 1], rec[:, 0]]
+    return a, b, tr

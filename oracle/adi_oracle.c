@@ -450,3 +450,126 @@ int oracle_num_threads_available(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------
+ * Wider problem class and the paper's literal sub-schemes.
+ * ------------------------------------------------------------------------ */
+
+/* Solve (I - kfac m Lap_dir) x = rhs along every line of direction dir
+ * (0: rows, spacing h1; 1: columns, spacing h2), i.e.
+ * -s_i x_{i-1} + (1 + 2 s_i) x_i - s_i x_{i+1} = rhs_i, s_i = kfac m_i / h^2. */
+static int sweep_coef(int dir, int nx, int ny, double h, double kfac, const double *m,
+                      const double *rhs_, double *out, int threads)
+{
+    int bad = 0;
+    int len = dir == 0 ? nx : ny;
+    int lines = dir == 0 ? ny : nx;
+    (void)threads;
+#pragma omp parallel num_threads(threads) reduction(| : bad)
+    {
+        double *a = (double *)malloc(sizeof(double) * (size_t)len * 7);
+        if (!a) { bad |= 2; } else {
+            double *b = a + len, *c = b + len, *d = c + len, *x = d + len, *cp = x + len, *dp = cp + len;
+#pragma omp for schedule(static)
+            for (int l = 0; l < lines; ++l) {
+                for (int t = 0; t < len; ++t) {
+                    size_t p = dir == 0 ? IDX(t, l, nx) : IDX(l, t, nx);
+                    double s = kfac * m[p] / (h * h);
+                    a[t] = -s; b[t] = 1.0 + 2.0 * s; c[t] = -s;
+                    d[t] = rhs_[p];
+                }
+                bad |= thomas_ws(len, a, b, c, d, x, cp, dp);
+                for (int t = 0; t < len; ++t) {
+                    size_t p = dir == 0 ? IDX(t, l, nx) : IDX(l, t, nx);
+                    out[p] = x[t];
+                }
+            }
+            free(a);
+        }
+    }
+    return bad;
+}
+
+/* One step of Eq. (CN1) with a time-dependent coefficient and a source
+ * field.  The coefficient of the Laplacian at level k is m^k = g_k m(x, y)
+ * (the paper's c(t) of Eq. f1 times the workloads' c^2(x, y)); CN1 weighs
+ * Lap u^{k+1} by m^{k+1}/2 and Lap u^{k-1} by m^{k-1}/2.  With
+ * z = u^{k+1} - 2u^k + u^{k-1} it reads exactly
+ *   (I - S Lap) z = tau^2 (g_{k+1} m Lap u^k
+ *                          + (g_{k-1} - g_{k+1})/2 m Lap u^{k-1} + f^k),
+ *   S = tau^2 g_{k+1} m / 2,
+ * and the ADI method factors I - S Lap into (I - S Lap_x)(I - S Lap_y) as in
+ * oracle_adi_step.  f^k = fk (a field, nullable) + wv / (h1 h2) at (sx, sy). */
+int oracle_adi_step_gen(int nx, int ny, double hx, double hy, double tau,
+                        const double *m, double g_prev, double g_next,
+                        const double *u_prev, const double *u_cur, const double *fk,
+                        double wv, int sx, int sy, double *u_next, int threads)
+{
+    size_t N = (size_t)nx * (size_t)ny;
+    double *r = (double *)malloc(sizeof(double) * N);
+    double *w = (double *)malloc(sizeof(double) * N);
+    double *z = (double *)malloc(sizeof(double) * N);
+    int rc = 0;
+    if (!r || !w || !z) { rc = 2; goto done; }
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            size_t p = IDX(i, j, nx);
+            double lc = lap_x_at(u_cur, nx, i, j, hx) + lap_y_at(u_cur, nx, ny, i, j, hy);
+            double lp = lap_x_at(u_prev, nx, i, j, hx) + lap_y_at(u_prev, nx, ny, i, j, hy);
+            double f = (fk ? fk[p] : 0.0) + ((i == sx && j == sy) ? wv / (hx * hy) : 0.0);
+            r[p] = tau * tau * (g_next * m[p] * lc + 0.5 * (g_prev - g_next) * m[p] * lp + f);
+        }
+    rc |= sweep_coef(0, nx, ny, hx, 0.5 * tau * tau * g_next, m, r, w, threads);
+    rc |= sweep_coef(1, nx, ny, hy, 0.5 * tau * tau * g_next, m, w, z, threads);
+    for (size_t p = 0; p < N; ++p) u_next[p] = 2.0 * u_cur[p] - u_prev[p] + z[p];
+done:
+    free(r); free(w); free(z);
+    return rc;
+}
+
+/* The two sub-problems of Section 2 taken literally, over half time levels
+ * (Algorithm 1: u, U0, Ux, Uy = u^{k-1/2}, u^k, u^{k+1/2}, u^{k+1}; after the
+ * step swap(u, Ux), swap(U0, Uy)).  Coefficient m (time-independent).
+ * variant 1, Eqs. fr1 and fr2 (S = tau^2 m / 2):
+ *   (I - S Lap_x) u^{k+1/2} = 2u^k - u^{k-1/2} + S Lap_x u^{k-1/2} + tau^2 f^k
+ *   (I - S Lap_y) u^{k+1}   = 2u^{k+1/2} - u^k + S Lap_y u^k + tau^2 f^{k+1/2}
+ * variant 2, the tridiagonal systems of Listing 1 (a = c = tau^2 m,
+ * b = 2 tau^2 m + h^2, right-hand side h^2 (u_old - 2 u^k) in the
+ * convention a y_{i-1} - b y_i + c y_{i+1} = f), the fully implicit form:
+ *   (I - tau^2 m Lap_x) u^{k+1/2} = 2u^k - u^{k-1/2} + tau^2 f^k
+ *   (I - tau^2 m Lap_y) u^{k+1}   = 2u^{k+1/2} - u^k + tau^2 f^{k+1/2}
+ * f^k = wv_k / (h1 h2), f^{k+1/2} = wv_half / (h1 h2) at (sx, sy) (the caller
+ * passes the half-level sample).  Outputs u_half = u^{k+1/2}, u_next = u^{k+1}. */
+int oracle_adi_step_halves(int variant, int nx, int ny, double hx, double hy, double tau,
+                           const double *m, const double *u_half_prev, const double *u_cur,
+                           double wv_k, double wv_half, int sx, int sy,
+                           double *u_half, double *u_next, int threads)
+{
+    if (variant != 1 && variant != 2) return 3;
+    size_t N = (size_t)nx * (size_t)ny;
+    double *r = (double *)malloc(sizeof(double) * N);
+    int rc = 0;
+    if (!r) return 2;
+    double kfac = variant == 1 ? 0.5 * tau * tau : tau * tau;
+    double alpha = variant == 1 ? 1.0 : 0.0;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            size_t p = IDX(i, j, nx);
+            double S = 0.5 * tau * tau * m[p];
+            double f = (i == sx && j == sy) ? wv_k / (hx * hy) : 0.0;
+            r[p] = 2.0 * u_cur[p] - u_half_prev[p] + alpha * S * lap_x_at(u_half_prev, nx, i, j, hx)
+                   + tau * tau * f;
+        }
+    rc |= sweep_coef(0, nx, ny, hx, kfac, m, r, u_half, threads);
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            size_t p = IDX(i, j, nx);
+            double S = 0.5 * tau * tau * m[p];
+            double f = (i == sx && j == sy) ? wv_half / (hx * hy) : 0.0;
+            r[p] = 2.0 * u_half[p] - u_cur[p] + alpha * S * lap_y_at(u_cur, nx, ny, i, j, hy)
+                   + tau * tau * f;
+        }
+    rc |= sweep_coef(1, nx, ny, hy, kfac, m, r, u_next, threads);
+    free(r);
+    return rc;
+}
