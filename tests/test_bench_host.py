@@ -54,3 +54,26 @@ def test_clock_samples_median_and_reasons():
         ["1500, 2070, 1400, 0x40, Not Active, Active, Not Active, Not Active"])
     assert hot["reasons"] == ["hw_thermal_slowdown"] and hot["sm_mhz"] == 1500.0
     assert bench.ClockSampler.parse([]) is None
+
+
+def test_gpus_two_starts_two_ranks_that_agree():
+    """`bench.py --gpus 2` outside torchrun starts two ranks itself (on
+    127.0.0.1); each sees WORLD_SIZE 2 and its own RANK."""
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2",
+                        "--print-ranks"], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [json.loads(ln) for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert sorted(d["rank"] for d in lines) == [0, 1]
+    assert all(d["world_size"] == 2 for d in lines)
+    assert sorted(d["local_rank"] for d in lines) == [0, 1]
+
+
+def test_custom_workload_needs_a_shape():
+    with pytest.raises(SystemExit):
+        bench.parse_args(["--workload", "custom"])
+    a = bench.parse_args(["--workload", "custom", "--nx", "64", "--ny", "32", "--time-steps", "3"])
+    p = bench.make_problem(bench.WORKLOADS["custom"], a)
+    assert (p.nx, p.ny, p.time_steps) == (64, 32, 3)
+    assert p.m.shape == (32, 64) and p.wavelet.shape == (5,)
+    assert p.tau == pytest.approx(0.5 / 65 / float(p.m.max()) ** 0.5)
