@@ -479,7 +479,7 @@ def run_single(ctx, prob):
     # the kernels the plan launches: the TMA-pipelined forms (stage 3) or the
     # one-CTA-per-tile forms
     xname = "x_pipe_kernel" if tun.get("x_stage") == 3 else "x_sweep_kernel"
-    yname = "y_pipe_kernel" if tun.get("y_stage") == 3 else "y_sweep_kernel"
+    yname = {3: "y_pipe_kernel", 4: "y_coop_kernel"}.get(tun.get("y_stage"), "y_sweep_kernel")
     roof = _roofline(kms, kcnt, {0: xname, 1: yname}, {0: BYTES_X * pts, 1: BYTES_Y * pts},
                      args.workload)
     roof["step_gbs_32B"] = 32.0 * pts * ts * args.steps / (max_ms / 1e3) / 1e9
@@ -620,15 +620,20 @@ def run_batch(ctx, steps=None):
     ctx_k["args"] = argparse.Namespace(**dict(vars(args), steps=K))
     _, kms, kcnt = _profiled(ctx_k, bench_step, B)
     roof = _roofline(kms, kcnt, {2: "batch_step_kernel"}, {2: 32 * pts})
-    # the plain single-grid kernels, one launch per shot and sweep, same work
-    B.set_mode(1)
-    for _ in range(2):
-        bench_step()
-    plain_ms, _, _, _ = _timed(ctx, bench_step, B.launch_count, steps=K, sample_clocks=False)
+    # the plain single-grid kernels, one launch per shot and sweep, same work:
+    # serially (mode 1) and as per-shot chains on parallel branches (mode 2)
+    other = {}
+    for mode in (1, 2):
+        B.set_mode(mode)
+        for _ in range(2):
+            bench_step()
+        ms_m, _, _, _ = _timed(ctx, bench_step, B.launch_count, steps=K, sample_clocks=False)
+        other[mode] = pts_all * ts * K / (ms_m / 1e3)
     B.set_mode(0)
+    B.sync_status()
     B.close()
     value = pts_all * ts * K / (max_ms / 1e3)
-    plain = pts_all * ts * K / (plain_ms / 1e3)
+    plain = other[1]
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": max_ms / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -639,7 +644,9 @@ def run_batch(ctx, steps=None):
                        "timed_launches": "one persistent launch per time step, step pairs "
                                          "replayed from CUDA graphs",
                        "parallelism": "shot-sharded" if world > 1 else "single GPU",
-                       "plain_per_shot_value": plain, "batched_over_plain": value / plain},
+                       "plain_per_shot_value": plain, "batched_over_plain": value / plain,
+                       "parallel_branches_value": other[2],
+                       "parallel_branches_over_plain": other[2] / plain},
             "roofline": roof, "gpu_launches": int(launches), "clocks": clk, "e2e": None,
             "cpu_baseline": None}
 

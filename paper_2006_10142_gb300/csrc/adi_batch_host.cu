@@ -112,6 +112,7 @@ int adi_wave::setup_batch(cudaStream_t st) {
 
 int adi_wave::enqueue_batch_step(cudaStream_t st) {
   const int n = (int)g.size();
+  if (batch_mode == 2) return enqueue_batch_steps_parallel(1, st);
   if (batch_mode == 1) {
     for (Grid& G : g) {
       int rc = launch_fwd(G, G.buf[G.cur], G.buf[1 - G.cur], G.w, nullptr, G.gd, st);
@@ -138,6 +139,50 @@ int adi_wave::enqueue_batch_step(cudaStream_t st) {
   for (Grid& G : g) {
     G.cur = 1 - G.cur;
     G.k += 1;
+    G.from_init = false;
+  }
+  return ADI_OK;
+}
+
+// Batch mode 2: every shot's steps are a chain of the single-grid kernels on
+// one of kBranches streams (shot s on branch s mod kBranches); the branches
+// fork from `st` and join back into it, so shots of different sizes overlap
+// and fill each other's tails, with no barrier between shots inside the
+// `nsteps` steps.
+int adi_wave::ensure_branches() {
+  if (fork_ev) return ADI_OK;
+  for (int b = 0; b < kBranches; ++b) {
+    CKB(cudaStreamCreateWithFlags(&branch[b], cudaStreamNonBlocking), "create branch stream");
+    CKB(cudaEventCreateWithFlags(&join_ev[b], cudaEventDisableTiming), "create join event");
+  }
+  CKB(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming), "create fork event");
+  return ADI_OK;
+}
+
+int adi_wave::enqueue_batch_steps_parallel(int nsteps, cudaStream_t st) {
+  int rc = ensure_branches();
+  if (rc != ADI_OK) return rc;
+  const int n = (int)g.size();
+  const int nb = std::min(n, (int)kBranches);
+  CKB(cudaEventRecord(fork_ev, st), "fork");
+  for (int b = 0; b < nb; ++b) CKB(cudaStreamWaitEvent(branch[b], fork_ev, 0), "branch wait");
+  for (int s = 0; s < n; ++s) {
+    Grid& G = g[s];
+    cudaStream_t bs = branch[s % nb];
+    int cur = G.cur;
+    for (int t = 0; t < nsteps; ++t) {
+      rc = launch_fwd(G, G.buf[cur], G.buf[1 - cur], G.w, nullptr, G.gd, bs);
+      if (rc != ADI_OK) return rc;
+      cur = 1 - cur;
+    }
+  }
+  for (int b = 0; b < nb; ++b) {
+    CKB(cudaEventRecord(join_ev[b], branch[b]), "join");
+    CKB(cudaStreamWaitEvent(st, join_ev[b], 0), "join wait");
+  }
+  for (Grid& G : g) {
+    if (nsteps & 1) G.cur = 1 - G.cur;
+    G.k += nsteps;
     G.from_init = false;
   }
   return ADI_OK;

@@ -54,15 +54,17 @@ cudaError_t adi::configure_current_device() {
 // up to 32 segments per column and two counters per strip, zeroed once.
 int adi_wave::ensure_ycoop(Grid& G) {
   if (G.plan.y_stage != ADI_STAGE_COOP) return ADI_OK;
+  const int cols = (G.nx + 31) / 32 * 32;
   const int strips = (G.nx + 15) / 16;
   G.yc.C = G.plan.C;
-  if (G.yc.tops != nullptr && G.yc.strips >= strips) return ADI_OK;
+  if (G.yc.tops != nullptr && G.yc.cols >= cols && G.yc.strips >= strips) return ADI_OK;
   cudaFree(G.yc.tops);
   cudaFree(G.yc.sync);
   G.yc.tops = nullptr;
   G.yc.sync = nullptr;
+  G.yc.cols = 0;
   G.yc.strips = 0;
-  cudaError_t e = cudaMalloc(&G.yc.tops, sizeof(float) * 8 * 16 * 32 * (size_t)strips);
+  cudaError_t e = cudaMalloc(&G.yc.tops, sizeof(float) * 8 * 32 * (size_t)cols);
   if (e == cudaSuccess) e = cudaMalloc(&G.yc.sync, sizeof(int) * 2 * (size_t)strips);
   if (e == cudaSuccess) e = cudaMemset(G.yc.sync, 0, sizeof(int) * 2 * (size_t)strips);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -75,6 +77,7 @@ int adi_wave::ensure_ycoop(Grid& G) {
     return fail(this, e == cudaErrorMemoryAllocation ? ADI_ENOMEM : ADI_ECUDA,
                 std::string("y sweep scratch: ") + cudaGetErrorString(e));
   }
+  G.yc.cols = cols;
   G.yc.strips = strips;
   return ADI_OK;
 }
@@ -160,8 +163,13 @@ int adi_wave::run_batch(int steps, const adi_source* src, cudaStream_t st) {
         for (Grid& G : g) { cur0.push_back(G.cur); k0.push_back(G.k); }
         const int64_t l0 = launches;
         CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "begin capture");
-        int rc = enqueue_batch_step(cap);
-        if (rc == ADI_OK) rc = enqueue_batch_step(cap);
+        int rc = ADI_OK;
+        if (batch_mode == 2) {
+          rc = enqueue_batch_steps_parallel(2, cap);  // per-shot chains of two steps
+        } else {
+          rc = enqueue_batch_step(cap);
+          if (rc == ADI_OK) rc = enqueue_batch_step(cap);
+        }
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(cap, &graph);
         for (size_t s = 0; s < g.size(); ++s) { g[s].cur = cur0[s]; g[s].k = k0[s]; }
@@ -659,6 +667,11 @@ adi_wave::~adi_wave() {
   if (d_shots) cudaFree(d_shots);
   if (d_items) cudaFree(d_items);
   if (d_sync) cudaFree(d_sync);
+  for (int b = 0; b < kBranches; ++b) {
+    if (branch[b]) cudaStreamDestroy(branch[b]);
+    if (join_ev[b]) cudaEventDestroy(join_ev[b]);
+  }
+  if (fork_ev) cudaEventDestroy(fork_ev);
   if (cap) cudaStreamDestroy(cap);
 }
 

@@ -58,7 +58,7 @@ struct Grid {
   int tm_lines = 0;                 // box height they were encoded with, 0 = none
   CUtensorMap ts_buf[2], ts_m, ts_w;  // strip maps (pipelined y sweep)
   int ts_rows = 0;                  // 64 * box rows + box columns they were encoded with, 0 = none
-  YCoop yc = {0, 0, nullptr, nullptr};  // scratch of the y sweep without clusters (y_stage 4)
+  YCoop yc = {0, 0, 0, nullptr, nullptr};  // scratch of the y sweep without clusters (y_stage 4)
 };
 
 // What adi_wave_adjoint needs to replay the last run.
@@ -132,7 +132,14 @@ struct adi_wave {
 
   // batched form (n_shots > 1)
   bool batch_fp64 = false;
-  int batch_mode = 0;                 // 0: persistent kernel, 1: plain kernels per shot
+  int batch_mode = 0;                 // 0: persistent kernel, 1: plain kernels per shot,
+                                      // 2: plain kernels per shot on parallel branches
+  static constexpr int kBranches = 8; // streams of batch mode 2
+  cudaStream_t branch[kBranches] = {};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[kBranches] = {};
+  int ensure_branches();
+  int enqueue_batch_steps_parallel(int nsteps, cudaStream_t st);
   adi::BatchShot* d_shots = nullptr;
   int2* d_items = nullptr;
   int n_items = 0;

@@ -62,6 +62,22 @@ def test_batch_matches_oracle_per_shot():
         assert rel_l2(got[b][0], o["u_prev"]) < 1e-4
 
 
+def test_parallel_branches_match_oracle_and_serial_launches():
+    """Batch mode 2 (each shot's steps a chain on one of eight streams,
+    replayed as parallel graph branches): per shot bit-exact with the serial
+    per-shot launches of mode 1 (the same kernels) and within 1e-4 of the
+    oracle; an odd step count exercises the graph pairs and a direct step."""
+    steps = 9
+    shots = _shots(SHAPES, steps, seed0=30)
+    a, _ = _run_batch(shots, steps, mode=2)
+    b, _ = _run_batch(shots, steps, mode=1)
+    for s, sh in enumerate(shots):
+        assert a[s][2] == steps + 1
+        assert np.array_equal(a[s][1], b[s][1]) and np.array_equal(a[s][0], b[s][0]), s
+        o = oracle_run(sh["m"], sh["phi"], sh["tau"], steps, src=sh["src"], wavelet=sh["wav"])
+        assert rel_l2(a[s][1], o["u_cur"]) < 1e-4
+
+
 def test_persistent_kernel_matches_per_shot_launches():
     steps = 9  # odd: four graph-replayed pairs and one direct step
     shots = _shots(SHAPES, steps, seed0=10)
