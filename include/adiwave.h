@@ -222,9 +222,11 @@ const char *adi_wave_last_error(const adi_wave *h);
  *                   persistent grid of co-resident CTAs takes (strip,
  *                   column segment) items and the segments of a column meet
  *                   through global memory, so long columns do not need
- *                   clusters of up to 16 CTAs; FP32 tree solver, 16
- *                   columns, chunk_y 32 with 256 or 512 threads or
- *                   chunk_y 16 with 512, at most 32 segments per column);
+ *                   clusters of up to 16 CTAs; FP32 tree solver; strips
+ *                   of 16 columns (chunk_y 32 with 256 or 512 threads,
+ *                   chunk_y 16 with 512) or 32 columns (512 threads,
+ *                   chunk_y 32 or 16); at most 32 segments per column;
+ *                   the automatic choice for columns of 8192 rows or more);
  * persist:          1 = one wave of resident CTAs (clusters) loops over the
  *                   tiles of each sweep and prefetches its next tile into L2
  *                   while solving the current one; -1 = one CTA per tile;
@@ -237,9 +239,10 @@ const char *adi_wave_last_error(const adi_wave *h);
  *                   by TMA tensor copies while the current rows are solved;
  *                   FP32 tree solver, rows of >= 256 floats); FP64
  *                   elimination always reads directly;
- * x_cluster:        ADI_STAGE_TMA only: 1 = one CTA per row, 2 = each row
- *                   split over a cluster of two CTAs (K = 32, one row per
- *                   CTA pair; two pairs fit an SM).
+ * x_cluster:        ADI_STAGE_TMA only: 1 = one CTA per row, 2 or 4 = each
+ *                   row split over a cluster of that many CTAs (K = 32, one
+ *                   row per cluster; 4: CTAs of 32..128 threads, four per
+ *                   SM).
  * Zero fields mean "choose automatically". */
 enum { ADI_STAGE_AUTO = 0, ADI_STAGE_SMEM = 1, ADI_STAGE_L2 = 2, ADI_STAGE_DIRECT = 2,
        ADI_STAGE_TMA = 3, ADI_STAGE_COOP = 4 /* y_stage only */ };
@@ -280,7 +283,11 @@ int adi_wave_profile_read(adi_wave *h, double *ms, int64_t *launches,
  * that hands out x-sweep and y-sweep work items of all shots from a global
  * queue (y items of a shot wait, bounded, for that shot's x items);
  * mode 1: the plain x and y kernels launched once per shot and step (the
- * comparison point).  ADI_EINVAL for other modes or single-grid handles. */
+ * comparison point);
+ * mode 2: the same plain kernels, each shot's steps a chain on one of eight
+ * streams that fork from and join into the caller's stream (parallel graph
+ * branches when replayed), so shots overlap one another's launches and tails.
+ * ADI_EINVAL for other modes or single-grid handles. */
 int adi_wave_set_batch_mode(adi_wave *h, int32_t mode);
 
 /* Failure-detection hook of the batched kernel.  spin_limit bounds the

@@ -105,9 +105,12 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
                          x_pipe_smem_bytes(spc, tsys, K, 1) <= (size_t)kMaxDynSmem;
     // a row split over a cluster of two CTAs (two pairs per SM): K = 32, one
     // row per CTA pair, at least 256 staged floats per CTA
-    const bool pair_ok = pipe_ok && K == 32 && spc == 1 && tsys >= 16 &&
+    const bool pair_ok = pipe_ok && K == 32 && spc == 1 && tsys >= 64 &&
                          x_pipe_smem_bytes(1, tsys / 2, K, 2) <= (size_t)kMaxDynSmem;
-    if (t.x_cluster < 0 || t.x_cluster > 2) { why = "x_cluster must be 0, 1 or 2"; return ADI_EINVAL; }
+    // four CTAs of at least one warp each (four per SM)
+    const bool quad_ok = pipe_ok && K == 32 && spc == 1 && tsys >= 128 && tsys <= 512 &&
+                         x_pipe_smem_bytes(1, tsys / 4, K, 4) <= (size_t)kMaxDynSmem;
+    if (t.x_cluster < 0 || t.x_cluster > 4 || t.x_cluster == 3) { why = "x_cluster must be 0, 1, 2 or 4"; return ADI_EINVAL; }
     const bool smem_ok = !P.fp64x &&
                          align64(x_smem_bytes(spc, tsys, P.fp64x, P.tree)) + x_stage_bytes(spc * tsys, K) <=
                              (size_t)kMaxDynSmem;
@@ -122,9 +125,12 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
     int xc = 1;
     if (xs == ADI_STAGE_TMA) {
       if (t.x_cluster == 2 && !pair_ok) { why = "x_cluster = 2 needs the TMA pipeline, K = 32 and one row per CTA"; return ADI_EUNSUPPORTED; }
-      // automatic: pairs for rows of 512 threads (16384 unknowns at K = 32)
+      if (t.x_cluster == 4 && !quad_ok) { why = "x_cluster = 4 needs the TMA pipeline, K = 32, one row per CTA and 128..512 threads per row"; return ADI_EUNSUPPORTED; }
+      // automatic: rows of 512 threads (16384 unknowns at K = 32) over four
+      // CTAs (measured 2 % faster than pairs at 16384^2), else pairs
       if (t.x_cluster == 2 || (t.x_cluster == 0 && pair_ok && tsys >= 512)) xc = 2;
-    } else if (t.x_cluster == 2) {
+      if (t.x_cluster == 4 || (t.x_cluster == 0 && quad_ok && tsys >= 512)) xc = 4;
+    } else if (t.x_cluster >= 2) {
       why = "x_cluster = 2 needs the TMA pipeline";
       return ADI_EUNSUPPORTED;
     }
@@ -187,30 +193,33 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
     if (t.y_stage < ADI_STAGE_AUTO || t.y_stage > ADI_STAGE_COOP) { why = "unknown y_stage"; return ADI_EINVAL; }
     int tcol, C;
     geom(K, tcol, C);
-    // Column segments joined through global memory (adi_ycoop.cu): chosen on
-    // request, or automatically where the cluster form needs clusters of 8
-    // or more CTAs (which leave SMs idle) or cannot hold the column at all.
-    // 16 columns; K = 32 with 256 threads (512 for columns beyond 16384
-    // rows) or K = 16 with 512; at most 32 segments per column.
-    if (t.y_stage == ADI_STAGE_COOP || t.y_stage == ADI_STAGE_AUTO) {
+    // Column segments joined through global memory (adi_ycoop.cu): strips of
+    // 16 columns (K = 32 with 256 or 512 threads; K = 16 with 512) or of 32
+    // columns (512 threads, K = 32 or 16); at most 32 segments per column.
+    // Chosen automatically for long columns (from 8192 rows, strips of 16,
+    // 512 threads: the cluster form needs clusters of 8 or 16 CTAs there and
+    // measured 3-6 % slower at 8192^2 and 16384^2).
+    const bool coop_auto = t.y_stage == ADI_STAGE_AUTO && t.chunk_y == 0 && cty == 0 &&
+                           (t.cols_per_cta == 0 || t.cols_per_cta == 16) && W == 16 &&
+                           !P.fp64y && P.tree && G.ny >= 8192;
+    if (t.y_stage == ADI_STAGE_COOP || coop_auto) {
+      const int cW = t.cols_per_cta ? t.cols_per_cta : 16;
       const int cK = t.chunk_y ? t.chunk_y : 32;
-      const int cthr = cty ? cty : ((cK == 32 && (G.ny + 511) / 512 <= 32) ? 256 : 512);
-      const int ctc = cthr / 16;
+      const int cthr = cty ? cty : 512;
+      const int ctc = cthr / cW;
       const int cC = (G.ny + ctc * cK - 1) / (ctc * cK);
-      const bool shape_ok = (cK == 32 && (cthr == 256 || cthr == 512)) || (cK == 16 && cthr == 512);
-      const bool coop_ok = !P.fp64y && P.tree && (t.cols_per_cta == 0 || t.cols_per_cta == 16) &&
-                           shape_ok && cC >= 1 && cC <= 32 && ctc * cK >= 64 &&
-                           y_coop_smem_bytes(ctc, cK, cC) <= (size_t)kMaxDynSmem;
-      if (t.y_stage == ADI_STAGE_COOP && !coop_ok) {
+      const bool shape_ok = cW == 16 ? ((cK == 32 && (cthr == 256 || cthr == 512)) || (cK == 16 && cthr == 512))
+                                     : (cW == 32 && cthr == 512 && (cK == 32 || cK == 16));
+      const bool coop_ok = !P.fp64y && P.tree && shape_ok && cC >= 1 && cC <= 32 && ctc * cK >= 64 &&
+                           y_coop_smem_bytes(cW, ctc, cK, cC) <= (size_t)kMaxDynSmem;
+      if (!coop_ok && !coop_auto) {
         why = "y segments through global memory not available for this shape";
         return ADI_EUNSUPPORTED;
       }
-      const bool want = t.y_stage == ADI_STAGE_COOP ||
-                        (coop_ok && W == 16 && t.chunk_y == 0 && cty == 0 && (!fits(K) || C >= 8));
-      if (want) {
+      if (coop_ok) {
         P.y_stage = ADI_STAGE_COOP;
         P.ky = cK;
-        P.log2W = 4;
+        P.log2W = ilog2(cW);
         P.log2tcol = ilog2(ctc);
         P.C = cC;
         goto y_done;
@@ -414,7 +423,7 @@ extern "C" int adi_wave_profile_read(adi_wave* h, double* ms, int64_t* launches,
 extern "C" int64_t adi_wave_launch_count(const adi_wave* h) { return h ? h->launches : 0; }
 
 extern "C" int adi_wave_set_batch_mode(adi_wave* h, int32_t mode) {
-  if (!h || h->g.size() < 2 || (mode != 0 && mode != 1)) return ADI_EINVAL;
+  if (!h || h->g.size() < 2 || mode < 0 || mode > 2) return ADI_EINVAL;
   h->batch_mode = mode;
   h->drop_graphs();
   return ADI_OK;

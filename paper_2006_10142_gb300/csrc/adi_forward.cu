@@ -31,7 +31,7 @@ namespace adi {
 // MAXT bounds the CTA size: 1024 caps a thread at 64 registers, 512 at 128,
 // 256 at 128 with two CTAs per SM; the launchers pick the smallest bound that
 // holds the CTA, so long chunks (K = 16, 32) keep their registers.
-constexpr int min_ctas(int maxt) { return maxt <= 256 ? 2 : 1; }
+constexpr int min_ctas(int maxt) { return maxt <= 128 ? 4 : maxt <= 256 ? 2 : 1; }
 
 template <int K, typename T, int MAXT, bool TREE>
 __global__ void __launch_bounds__(MAXT, min_ctas(MAXT)) x_sweep_kernel(const XArgs a) {
@@ -91,8 +91,8 @@ __device__ __forceinline__ float stage_at(const float* row, int e) {
   return row[(swz4(e >> 2) << 2) | (e & 3)];
 }
 
-// XC = 2: each row is split over a cluster of two CTAs (rank r stages and
-// solves columns [r rowf, (r + 1) rowf)); one row per CTA pair.
+// XC = 2 or 4: each row is split over a cluster of XC CTAs (rank r stages
+// and solves columns [r rowf, (r + 1) rowf)); one row per cluster.
 template <int K, int MAXT, int XC>
 __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
     x_pipe_kernel(const XArgs a, const __grid_constant__ CUtensorMap tm_u,
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
   constexpr int NQ = K / 4;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  const int rank = XC == 2 ? cluster_rank(2) : 0;
+  const int rank = XC > 1 ? cluster_rank(XC) : 0;
   const int tsys = 1 << a.log2tsys;        // threads per row in this CTA
   const int rowf = tsys * K;               // floats per staged row (a power of two >= 256)
   const int coff = rank * rowf;            // first column of this CTA's part of the row
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
   const int nblk = (a.ny + a.spc - 1) / a.spc;
   // L2 prefetch of halo rows: this CTA's part of the row, inside the pitch
   const uint32_t pf_bytes =
-      XC == 2 ? (uint32_t)(min(rowf, a.ld - coff) * 4) : (uint32_t)((a.nx * 4 + 15) & ~15);
+      XC > 1 ? (uint32_t)(max(0, min(rowf, a.ld - coff)) * 4) : (uint32_t)((a.nx * 4 + 15) & ~15);
 
   if (tid == 0) {
     mbar_init(bar, 1);
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
     }
   };
   const int blk0 = (int)blockIdx.x / XC;
-  const int nrun = (int)gridDim.x / XC;  // CTAs (XC = 1) or CTA pairs (XC = 2) in the grid
+  const int nrun = (int)gridDim.x / XC;  // CTAs (XC = 1) or clusters (XC > 1) in the grid
   if (tid < 32 && blk0 < nblk) issue(blk0);
 
   const int sys = tid >> a.log2tsys;
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
   uint32_t phase = 0;
   bool timed_out = false;
   for (int blk = blk0; blk < nblk; blk += nrun) {
-    if constexpr (XC == 2) cluster_arrive_early(2);
+    if constexpr (XC > 1) cluster_arrive_early(XC);
    if (coalesced_halo) {
     // The halo rows u^k_{j-1} + u^k_{j+1} of the block's rows, read with
     // coalesced float4 loads (consecutive lanes, consecutive 16-byte groups)
@@ -256,13 +256,13 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
     if (tid < 32 && next < nblk) {
       fence_proxy_async_smem();
       issue(next);
-      if (lane == 0) {
+      if (lane == 0 && pf_bytes > 0) {  // (a cluster rank wholly past the pitch prefetches nothing)
         const int jl = next * a.spc - 1, jh = next * a.spc + a.spc;
         if (jl >= 0) l2_prefetch_bulk(a.u + (size_t)jl * a.ld + coff, pf_bytes);
         if (jh < a.ny) l2_prefetch_bulk(a.u + (size_t)jh * a.ld + coff, pf_bytes);
       }
     }
-    if constexpr (XC == 2) x_solve_row_pair<K>(smem, rank, d, s);
+    if constexpr (XC > 1) x_solve_row_split<K, XC>(smem, rank, d, s);
     else x_solve_rows<K, float, true>(smem, a.spc, a.log2tsys, a.pcr, sys, p, d, s);
     // w through the swizzled stage, stored by TMA boxes
 #pragma unroll
@@ -275,13 +275,15 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
       const int nrows = min(a.spc, a.ny - j0);
       for (int t = lane; t < nrows * nchunk; t += 32) {
         const int r = t / nchunk, c = t - r * nchunk;
-        tma_store_3d(&tm_w, 0, c * L + rank * lines, j0 + r, st_w + (uint32_t)((r * rowf + c * L * 32) * 4));
+        // boxes that start past the pitch (a cluster rank beyond the row) are not stored
+        if ((c * L + rank * lines) * 32 < a.ld)
+          tma_store_3d(&tm_w, 0, c * L + rank * lines, j0 + r, st_w + (uint32_t)((r * rowf + c * L * 32) * 4));
       }
       bulk_commit();
     }
   }
   if (tid < 32) bulk_wait_all();
-  if constexpr (XC == 2) cgx::this_cluster().sync();  // no CTA leaves while its shared memory may be written
+  if constexpr (XC > 1) cgx::this_cluster().sync();  // no CTA leaves while its shared memory may be written
   if (timed_out && (tid & 31) == 0 && a.err) atomicOr(a.err, ERR_TIMEOUT);
 }
 
@@ -590,11 +592,11 @@ size_t y_smem_bytes(int W, int C, int tcol, bool fp64, bool tree) {
 
 size_t y_stage_bytes(int threads, int K) { return align64((size_t)2 * K * threads * sizeof(float)); }
 size_t x_stage_bytes(int threads, int K) { return align64((size_t)2 * K * threads * sizeof(float)); }
-// tsys = threads per row in one CTA; xc = 2: the solver region holds the
-// warp summaries of both CTAs of a pair.
+// tsys = threads per row in one CTA; xc > 1: the solver region holds the
+// warp summaries of all CTAs of the cluster.
 static size_t x_pipe_tree_bytes(int spc, int tsys, int xc) {
-  return xc == 2 ? XTreeSmem<float>::bytes(2 * std::max(1, spc * tsys / 32))
-                 : x_smem_bytes(spc, tsys, false, true);
+  return xc > 1 ? XSplitSmem::bytes(std::max(1, spc * tsys / 32), xc)
+                : x_smem_bytes(spc, tsys, false, true);
 }
 
 size_t x_pipe_smem_bytes(int spc, int tsys, int K, int xc) {
@@ -705,9 +707,11 @@ template <int K, int MAXT, int XC>
 static cudaError_t launch_x_pipe_t(const XArgs& a_in, const CUtensorMap& tu, const CUtensorMap& tm,
                                    const CUtensorMap& tw, cudaStream_t st) {
   XArgs a = a_in;
-  if (XC == 2) {  // the plan's threads per row are split over the pair
-    if (a.spc != 1 || a.log2tsys < 6) return cudaErrorInvalidValue;
-    a.log2tsys -= 1;
+  if (XC > 1) {  // the plan's threads per row are split over the cluster
+    const int l2 = XC == 2 ? 1 : 2;
+    if (a.spc != 1 || a.log2tsys < 5 + l2) return cudaErrorInvalidValue;
+    a.log2tsys -= l2;
+    if ((XC << a.log2tsys) / 32 > 32) return cudaErrorInvalidValue;  // top system of one warp
   }
   const int tsys = 1 << a.log2tsys;
   const int threads = a.spc * tsys;
@@ -750,6 +754,7 @@ cudaError_t launch_x_pipe(const XArgs& a, int K, const CUtensorMap& tu, const CU
                           const CUtensorMap& tw, cudaStream_t st) {
   const int threads = a.spc << a.log2tsys;
   if (a.xc == 2) return K == 32 ? launch_x_pipe_t<32, 256, 2>(a, tu, tm, tw, st) : cudaErrorInvalidValue;
+  if (a.xc == 4) return K == 32 ? launch_x_pipe_t<32, 128, 4>(a, tu, tm, tw, st) : cudaErrorInvalidValue;
   switch (K) {
     case 8: return launch_x_pipe_t<8, 1024, 1>(a, tu, tm, tw, st);
     case 16:
@@ -776,14 +781,14 @@ int y_pipe_box_rows(int tcol, int K) {
 }
 
 // Tensor map of a pitched [ny][ld] FP32 field as 2D {ld, ny}, boxes of
-// {box_cols, box_rows} (box_cols = 4, 8 or 16), no swizzle, zero fill outside.
+// {box_cols, box_rows} (box_cols = 4, 8, 16 or 32), no swizzle, zero fill outside.
 cudaError_t encode_strip_map(CUtensorMap* out, const float* base, int ld, int ny, int box_cols,
                              int box_rows) {
   EncodeTiledFn fn = nullptr;
   cudaError_t e = get_encode_fn(&fn);
   if (e != cudaSuccess) return e;
   if (ld % 32 != 0 || box_rows < 1 || box_rows > 256 || ((uintptr_t)base & 15) != 0 ||
-      (box_cols != 4 && box_cols != 8 && box_cols != 16))
+      (box_cols != 4 && box_cols != 8 && box_cols != 16 && box_cols != 32))
     return cudaErrorInvalidValue;
   const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)ny};
   const cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
@@ -949,6 +954,7 @@ cudaError_t configure_kernels() {
   if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<32, 256, 1>, false);
   if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<32, 512, 1>, false);
   if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<32, 256, 2>, true);
+  if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<32, 128, 4>, true);
   return e;
 }
 

@@ -98,11 +98,12 @@ cudaError_t launch_y_pipe_adj(const YArgs& a, int K, const CUtensorMap& lam, con
 // global memory.  Scratch of one grid:
 struct YCoop {
   int C;        // segments per column (1..32)
-  int strips;   // strips of 16 columns the scratch holds
-  float* tops;  // [strips][16][C] segment summaries, 8 floats each
+  int cols;     // columns the summaries hold (nx rounded up to 32)
+  int strips;   // strips the counters hold (nx / 16 rounded up)
+  float* tops;  // [cols][C] segment summaries, 8 floats each
   int* sync;    // [strips][2] arrival / completion counters, zero between launches
 };
-size_t y_coop_smem_bytes(int tcol, int K, int C);
+size_t y_coop_smem_bytes(int W, int tcol, int K, int C);
 int y_coop_segments(int ny, int tcol, int K);
 cudaError_t launch_y_coop(const YArgs& a, int K, const YCoop& yc, const YMaps& mp, cudaStream_t st);
 cudaError_t launch_y_coop_adj(const YArgs& a, int K, const YCoop& yc, const CUtensorMap& lam,

@@ -295,41 +295,53 @@ __device__ __forceinline__ void y_solve_cols(unsigned char* smem, int log2W, int
 }
 
 // ---------------------------------------------------------------------------
-// x (row) solve of one row split over a cluster of two CTAs (FP32, tree
-// solver): rank 0 holds the first half of the row, rank 1 the second, each
-// thread K consecutive unknowns.  Every CTA writes its warp summaries to both
-// CTAs; after one cluster barrier each CTA solves the top system (2 x warps
-// segments) itself and reads its end values locally.  The caller executes
-// cluster_arrive_early(2) once per row (the next row's wait orders this row's
-// reads of `tops` before they are overwritten) and synchronises the cluster
-// before exit.  Shared memory: XTreeSmem<float> sized for 2 x warps; at most
-// 16 warps per CTA.
+// x (row) solve of one row split over a cluster of XC CTAs (FP32, tree
+// solver): rank r holds the r-th part of the row, each thread K consecutive
+// unknowns.  Every CTA writes its warp summaries to all XC CTAs over DSMEM;
+// after one cluster barrier each CTA solves the top system (XC x warps
+// segments, at most 32) itself and reads its end values locally.  The caller
+// executes cluster_arrive_early(XC) once per row (the next row's wait orders
+// this row's reads of `tops` before they are overwritten) and synchronises
+// the cluster before exit.  Shared memory: XSplitSmem.
 // ---------------------------------------------------------------------------
-template <int K>
-__device__ __forceinline__ void x_solve_row_pair(unsigned char* smem, int rank, float (&d)[K],
-                                                 float (&s)[K]) {
+struct XSplitSmem {
+  // nodes[nw][31] (this CTA's warps) | tops[XC * nw] | xtop[XC * nw][2]
+  static __host__ __device__ size_t off_tops(int nw) {
+    return align64((size_t)nw * 31 * sizeof(Node<float>));
+  }
+  static __host__ __device__ size_t off_xtop(int nw, int xc) {
+    return off_tops(nw) + align64((size_t)xc * nw * sizeof(Seg<float>));
+  }
+  static __host__ __device__ size_t bytes(int nw, int xc) {
+    return off_xtop(nw, xc) + align64((size_t)xc * nw * 2 * sizeof(float));
+  }
+};
+
+template <int K, int XC>
+__device__ __forceinline__ void x_solve_row_split(unsigned char* smem, int rank, float (&d)[K],
+                                                  float (&s)[K]) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
   Node<float>* nodes = reinterpret_cast<Node<float>*>(smem) + warp * 31;
-  Seg<float>* tops = reinterpret_cast<Seg<float>*>(smem + XTreeSmem<float>::off_tops(2 * nw));
-  float* xtop = reinterpret_cast<float*>(smem + XTreeSmem<float>::off_xtop(2 * nw));
+  Seg<float>* tops = reinterpret_cast<Seg<float>*>(smem + XSplitSmem::off_tops(nw));
+  float* xtop = reinterpret_cast<float*>(smem + XSplitSmem::off_xtop(nw, XC));
   Seg<float> S;
   Node<float> ndc;
   chunk_reduce_split<K, float>(d, s, S, ndc);
   S = warp_tree_up<float>(S, nodes, lane, 5);  // every lane holds the warp's summary
   cgx::cluster_group cl = cgx::this_cluster();
-  cluster_wait_started(2);
-  if (lane < 2) *cl.map_shared_rank(tops + rank * nw + warp, lane) = S;
+  cluster_wait_started(XC);
+  if (lane < XC) *cl.map_shared_rank(tops + rank * nw + warp, lane) = S;
   cl.sync();
   if (warp == 0) {
     Eq<float> E0 = eq_identity<float>(), E1 = eq_identity<float>();
-    if (lane < 2 * nw) {
+    if (lane < XC * nw) {
       E0 = tops[lane].f;
       E1 = tops[lane].l;
     }
-    pcr64<float>(E0, E1, lane, 4 * nw);
-    if (lane < 2 * nw) {
+    pcr64<float>(E0, E1, lane, 2 * XC * nw);
+    if (lane < XC * nw) {
       xtop[2 * lane] = div_t(E0.d, E0.b);
       xtop[2 * lane + 1] = div_t(E1.d, E1.b);
     }

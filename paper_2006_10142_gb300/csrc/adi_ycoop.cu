@@ -7,21 +7,23 @@
 // A column of 16384 rows then needs clusters of 16 CTAs, of which only 7
 // fit the GPU at a time (112 of 152 SMs).  Here the CTAs of a strip are
 // independent CTAs of one persistent grid:
-//   - work item = (strip of 16 columns, segment of R = tcol * K rows); the
+//   - work item = (strip of W = 16 or 32 columns, segment of R = tcol * K rows); the
 //     grid's CTAs, all resident (cooperative launch), take items in
 //     increasing order, item = strip * C + segment;
 //   - each CTA reduces its segment of every column to a two-equation
 //     summary (per-thread partition, then block cyclic reduction over the
 //     column's chunks by warp shuffles, as in y_solve_cols) and writes it to
 //     global memory;
-//   - once all C segments of the strip have arrived (one counter per strip,
-//     release / acquire at GPU scope, bounded wait), every CTA of the strip
-//     solves the top systems of all 16 columns itself (one warp per column,
+//   - once all C segments of the strip have arrived (one counter per strip:
+//     a release-add per column summary, an acquire poll with a bounded
+//     wait), every CTA of the strip
+//     solves the top systems of all W columns itself (one warp per column,
 //     parallel cyclic reduction of 2C equations), so one round trip through
 //     L2 per item suffices, and unwinds its own segment;
 //   - the TMA pipeline of y_pipe_kernel is kept: the next item's w and m
-//     tiles stream into shared memory while the current item is solved, and
-//     its u^k, u^{k-1} boxes are prefetched into L2.
+//     tiles stream into shared memory while the current item is solved; the
+//     current item's u^k, u^{k-1} boxes are prefetched into L2 when its
+//     solve starts.
 // Every wait ends: a CTA waits only for the items of its own strip, and the
 // lowest-numbered waiting item's missing strip-mates are either running or
 // queued behind lower-numbered items on resident CTAs that do not wait for
@@ -40,6 +42,10 @@
 
 namespace adi {
 
+__device__ __forceinline__ void red_release_gpu_add(int* p, int v) {
+  asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ int ld_acquire_gpu(const int* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -53,27 +59,26 @@ struct YCoopLayout {
   size_t bytes;
 };
 
-__host__ __device__ inline YCoopLayout y_coop_layout(int tcol, int K, int C) {
-  const int threads = 16 * tcol;
+__host__ __device__ inline YCoopLayout y_coop_layout(int W, int tcol, int K, int C) {
+  const int threads = W * tcol;
   YCoopLayout L;
   size_t off = align64((size_t)threads * sizeof(Seg<float>));  // chunk summaries / end values
   L.off_nodes = (int)off;
   off += align64((size_t)(threads / 32) * 31 * sizeof(Node<float>));
   L.off_xtop = (int)off;
-  off += align64((size_t)16 * C * 2 * sizeof(float));         // top-system solutions
+  off += align64((size_t)W * C * 2 * sizeof(float));          // top-system solutions
   L.off_bar = (int)off;
-  off += 8 + 128 + (size_t)2 * tcol * K * 16 * sizeof(float);  // mbarrier, w and m tiles
+  off += 8 + 128 + (size_t)2 * tcol * K * W * sizeof(float);   // mbarrier, w and m tiles
   L.bytes = off;
   return L;
 }
 
-template <int K, int MAXT, bool ADJ>
+template <int K, int MAXT, int W, bool ADJ>
 __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 2 : 1)
     y_coop_kernel(const YArgs a, const YCoop yc, const __grid_constant__ CUtensorMap tm_w,
                   const __grid_constant__ CUtensorMap tm_m, const __grid_constant__ CUtensorMap tm_uc,
                   const __grid_constant__ CUtensorMap tm_up) {
-  constexpr int W = 16;
-  constexpr int QG = 32 / W;  // row groups (q) per warp
+  constexpr int QG = 32 / W;  // row groups (q) per warp (W = 16 or 32)
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -87,7 +92,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 2 : 1)
   const int nbox = R / BH;
   const int nstrips = (a.nx + W - 1) / W;
   const int nitems = nstrips * C;
-  const YCoopLayout Lo = y_coop_layout(tcol, K, C);
+  const YCoopLayout Lo = y_coop_layout(W, tcol, K, C);
   Seg<float>* csum = reinterpret_cast<Seg<float>*>(smem);
   Node<float>* nodes = reinterpret_cast<Node<float>*>(smem + Lo.off_nodes) + warp * 31;
   float* xtop = reinterpret_cast<float*>(smem + Lo.off_xtop);
@@ -104,19 +109,27 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 2 : 1)
     mbar_fence_init();
   }
   __syncthreads();
-  // warp 0: the TMA boxes of item `it` (one box per lane) and the L2
-  // prefetch of its u boxes
+  // warp 0: the TMA boxes of item `it` (one box per lane)
   auto issue = [&](int it) {
     const int strip = it / C, seg = it - (it / C) * C;
     const int row0 = seg * R;
     if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(2 * R * W * 4));
-    constexpr int NF = ADJ ? 2 : 4;  // operations per box
-    for (int t = lane; t < NF * nbox; t += 32) {
-      const int b = t / NF, f = t % NF;
+    for (int t = lane; t < 2 * nbox; t += 32) {
+      const int b = t >> 1;
       const uint32_t off = (uint32_t)(b * BH * W * 4);
-      if (f == 0) tma_load_2d(st_w + off, &tm_w, strip * W, row0 + b * BH, bar);
-      else if (f == 1) tma_load_2d(st_m + off, &tm_m, strip * W, row0 + b * BH, bar);
-      else if (f == 2) tma_prefetch_2d(&tm_uc, strip * W, row0 + b * BH);
+      if ((t & 1) == 0) tma_load_2d(st_w + off, &tm_w, strip * W, row0 + b * BH, bar);
+      else tma_load_2d(st_m + off, &tm_m, strip * W, row0 + b * BH, bar);
+    }
+  };
+  // warp 0: L2 prefetch of the u^k and u^{k-1} boxes item `it` updates --
+  // issued when the item's solve starts, so that they arrive during the
+  // solve and the wait for the strip and are not evicted before the update
+  auto prefetch_u = [&](int it) {
+    const int strip = it / C, seg = it - (it / C) * C;
+    const int row0 = seg * R;
+    for (int t = lane; t < 2 * nbox; t += 32) {
+      const int b = t >> 1;
+      if ((t & 1) == 0) tma_prefetch_2d(&tm_uc, strip * W, row0 + b * BH);
       else tma_prefetch_2d(&tm_up, strip * W, row0 + b * BH);
     }
   };
@@ -177,12 +190,6 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 2 : 1)
         s[g + r] = colok ? sc * vm[r] : 0.f;
       }
     }
-    __syncthreads();  // the stage is consumed: refill it with the next item
-    const int next = item + (int)gridDim.x;
-    if (tid < 32 && next < nitems) {
-      fence_proxy_async_smem();
-      issue(next);
-    }
     // 1. partition: each thread's K rows to a two-equation summary
     Node<float> ndc;
     {
@@ -190,9 +197,19 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 2 : 1)
       chunk_reduce_split<K, float>(d, s, S, ndc);
       csum[col * tcol + q] = S;
     }
-    __syncthreads();
+    __syncthreads();  // the summaries are in place and the stage is consumed: refill it
+    const int next = item + (int)gridDim.x;
+    if (tid < 32) {
+      if (!ADJ) prefetch_u(item);
+      if (next < nitems) {
+        fence_proxy_async_smem();
+        issue(next);
+      }
+    }
     // 2. the segment of each column to one summary (tree over its chunks),
-    // to global memory; arrive on the strip's counter
+    // to global memory; the lane that stores a column's summary arrives on
+    // the strip's counter with release semantics (its own store first), so
+    // the counter reaches C * W when every summary of the strip is visible
     {
       Seg<float> S = csum[tc * tcol + chunk];
       S = warp_tree_up<float>(S, nodes, lane, lg);
@@ -200,17 +217,15 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 2 : 1)
         float4* dst = reinterpret_cast<float4*>(yc.tops + (((size_t)strip * W + tc) * C + seg) * 8);
         __stcg(dst, make_float4(S.f.a, S.f.b, S.f.c, S.f.d));
         __stcg(dst + 1, make_float4(S.l.a, S.l.b, S.l.c, S.l.d));
-        __threadfence();
+        red_release_gpu_add(yc.sync + 2 * strip, 1);
       }
     }
-    __syncthreads();
     if (tid == 0) {
-      int* cnt = yc.sync + 2 * strip;
-      __threadfence();
-      atomicAdd(cnt, 1);
-      if (ld_acquire_gpu(cnt) < C) {
+      const int* cnt = yc.sync + 2 * strip;
+      const int target = C * W;
+      if (ld_acquire_gpu(cnt) < target) {
         const uint64_t t0 = global_ns();
-        while (ld_acquire_gpu(cnt) < C) {
+        while (ld_acquire_gpu(cnt) < target) {
           if (global_ns() - t0 > 1000000000ull) {
             timed_out = true;
             break;
@@ -311,27 +326,31 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 2 : 1)
   if (__any_sync(0xffffffffu, timed_out) && (tid & 31) == 0 && a.err) atomicOr(a.err, ERR_TIMEOUT);
 }
 
-size_t y_coop_smem_bytes(int tcol, int K, int C) { return y_coop_layout(tcol, K, C).bytes; }
+size_t y_coop_smem_bytes(int W, int tcol, int K, int C) { return y_coop_layout(W, tcol, K, C).bytes; }
 
 int y_coop_segments(int ny, int tcol, int K) { return (ny + tcol * K - 1) / (tcol * K); }
 
-template <int K, int MAXT, bool ADJ>
+template <int K, int MAXT, int W, bool ADJ>
 static cudaError_t launch_y_coop_t(const YArgs& a, const YCoop& yc, const YMaps& mp, cudaStream_t st) {
   const int tcol = 1 << a.log2tcol;
-  const int threads = 16 * tcol;
-  if (a.log2W != 4 || threads != MAXT || tcol > 32 || tcol * K < 64) return cudaErrorInvalidValue;
+  const int threads = W * tcol;
+  if ((1 << a.log2W) != W || threads != MAXT || tcol > 32 || tcol * K < 64) return cudaErrorInvalidValue;
   if (yc.C < 1 || yc.C > 32 || yc.C != y_coop_segments(a.ny, tcol, K)) return cudaErrorInvalidValue;
-  if (yc.tops == nullptr || yc.sync == nullptr || yc.strips < (a.nx + 15) / 16) return cudaErrorInvalidValue;
-  const size_t sm = y_coop_smem_bytes(tcol, K, yc.C);
+  // scratch: summaries of every column (rounded up to the strip) and two
+  // counters per strip
+  const int strips = (a.nx + W - 1) / W;
+  if (yc.tops == nullptr || yc.sync == nullptr || yc.cols < strips * W || yc.strips < strips)
+    return cudaErrorInvalidValue;
+  const size_t sm = y_coop_smem_bytes(W, tcol, K, yc.C);
   if (sm > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
-  auto kern = y_coop_kernel<K, MAXT, ADJ>;
+  auto kern = y_coop_kernel<K, MAXT, W, ADJ>;
   int dev = 0, nsm = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, sm);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const int nitems = ((a.nx + 15) / 16) * yc.C;
+  const int nitems = strips * yc.C;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(std::max(1, std::min(nitems, nsm * per_sm)), 1, 1);
   cfg.blockDim = dim3(threads, 1, 1);
@@ -348,10 +367,13 @@ static cudaError_t launch_y_coop_t(const YArgs& a, const YCoop& yc, const YMaps&
 template <bool ADJ>
 static cudaError_t launch_y_coop_any(const YArgs& a, int K, const YCoop& yc, const YMaps& mp,
                                      cudaStream_t st) {
-  const int threads = 16 << a.log2tcol;
-  if (K == 32 && threads == 256) return launch_y_coop_t<32, 256, ADJ>(a, yc, mp, st);
-  if (K == 32 && threads == 512) return launch_y_coop_t<32, 512, ADJ>(a, yc, mp, st);
-  if (K == 16 && threads == 512) return launch_y_coop_t<16, 512, ADJ>(a, yc, mp, st);
+  const int W = 1 << a.log2W;
+  const int threads = W << a.log2tcol;
+  if (W == 16 && K == 32 && threads == 256) return launch_y_coop_t<32, 256, 16, ADJ>(a, yc, mp, st);
+  if (W == 16 && K == 32 && threads == 512) return launch_y_coop_t<32, 512, 16, ADJ>(a, yc, mp, st);
+  if (W == 16 && K == 16 && threads == 512) return launch_y_coop_t<16, 512, 16, ADJ>(a, yc, mp, st);
+  if (W == 32 && K == 32 && threads == 512) return launch_y_coop_t<32, 512, 32, ADJ>(a, yc, mp, st);
+  if (W == 32 && K == 16 && threads == 512) return launch_y_coop_t<16, 512, 32, ADJ>(a, yc, mp, st);
   return cudaErrorInvalidValue;
 }
 
@@ -375,12 +397,16 @@ static cudaError_t allow(const void* kern) {
 }
 
 cudaError_t configure_y_coop_kernels() {
-  cudaError_t e = allow((const void*)y_coop_kernel<32, 256, false>);
-  if (e == cudaSuccess) e = allow((const void*)y_coop_kernel<32, 256, true>);
-  if (e == cudaSuccess) e = allow((const void*)y_coop_kernel<32, 512, false>);
-  if (e == cudaSuccess) e = allow((const void*)y_coop_kernel<32, 512, true>);
-  if (e == cudaSuccess) e = allow((const void*)y_coop_kernel<16, 512, false>);
-  if (e == cudaSuccess) e = allow((const void*)y_coop_kernel<16, 512, true>);
+  cudaError_t e = cudaSuccess;
+#define ADI_COOP_CFG(K, T, W)                                                        \
+  if (e == cudaSuccess) e = allow((const void*)y_coop_kernel<K, T, W, false>);       \
+  if (e == cudaSuccess) e = allow((const void*)y_coop_kernel<K, T, W, true>);
+  ADI_COOP_CFG(32, 256, 16)
+  ADI_COOP_CFG(32, 512, 16)
+  ADI_COOP_CFG(16, 512, 16)
+  ADI_COOP_CFG(32, 512, 32)
+  ADI_COOP_CFG(16, 512, 32)
+#undef ADI_COOP_CFG
   return e;
 }
 

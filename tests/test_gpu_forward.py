@@ -248,10 +248,11 @@ def test_staging_modes_match_oracle(nx, ny, xs, ys):
 
 
 @pytest.mark.parametrize("nx,ny", [(16384, 9), (12000, 33), (9000, 20), (2500, 40)])
-@pytest.mark.parametrize("xc", [1, 2])
+@pytest.mark.parametrize("xc", [1, 2, 4])
 def test_row_split_over_cta_pair_matches_oracle(nx, ny, xc):
-    """Rows solved by one CTA or split over a cluster of two (the halves
-    meet through DSMEM), including rows whose second half is mostly padding."""
+    """Rows solved by one CTA or split over a cluster of two or four (the
+    parts meet through DSMEM), including rows whose last parts are mostly or
+    wholly padding."""
     steps = 4
     m, phi, tau, src, wav = _problem(nx, ny, steps, seed=nx % 97 + ny)
     tun = dict(x_stage=3, chunk_x=32, x_cluster=xc, rows_per_cta=1)
@@ -262,33 +263,23 @@ def test_row_split_over_cta_pair_matches_oracle(nx, ny, xc):
     assert rel_l2(g["u_prev"], o["u_prev"]) < TOL
 
 
-@pytest.mark.parametrize("nx,ny,ky,ty", [(40, 5000, 32, 256), (300, 1500, 32, 512),
-                                         (1100, 9000, 32, 256), (77, 16384, 32, 256),
-                                         (33, 32768, 32, 512), (50, 2049, 16, 512),
-                                         (17, 64, 32, 256)])
-def test_y_segments_through_global_memory_match_oracle(nx, ny, ky, ty):
+@pytest.mark.parametrize("nx,ny,W,ky,ty", [(40, 5000, 16, 32, 256), (300, 1500, 16, 32, 512),
+                                           (1100, 9000, 16, 32, 256), (77, 16384, 16, 32, 256),
+                                           (33, 32768, 16, 32, 512), (50, 2049, 16, 16, 512),
+                                           (17, 64, 16, 32, 256), (100, 5000, 32, 32, 512),
+                                           (1100, 16384, 32, 32, 512), (70, 3000, 32, 16, 512)])
+def test_y_segments_through_global_memory_match_oracle(nx, ny, W, ky, ty):
     """The y sweep without clusters (y_stage 4): persistent co-resident CTAs
-    whose column segments meet through global memory; one segment per column
-    (17 x 64), up to 32 segments (16384 rows at 512 per segment, 32768 at
-    1024), partial last segments and strips past nx."""
+    whose column segments meet through global memory; strips of 16 and 32
+    columns, one segment per column (17 x 64), up to 32 segments (16384 rows
+    at 512 per segment, 32768 at 1024), partial last segments and strips past
+    nx; the run replays step pairs from a CUDA graph."""
     steps = 6
     m, phi, tau, src, wav = _problem(nx, ny, steps, seed=nx + ny)
-    tun = dict(y_stage=4, chunk_y=ky, cta_threads_y=ty, cols_per_cta=16)
+    tun = dict(y_stage=4, chunk_y=ky, cta_threads_y=ty, cols_per_cta=W)
     g = gpu_run(m, phi, tau, steps, src=src, wavelet=wav, tuning=tun)
     assert g["tuning"]["y_stage"] == 4 and g["tuning"]["chunk_y"] == ky
-    o = oracle_run(m, phi, tau, steps, src=src, wavelet=wav)
-    assert rel_l2(g["u_cur"], o["u_cur"]) < TOL
-    assert rel_l2(g["u_prev"], o["u_prev"]) < TOL
-
-
-def test_default_plan_takes_global_segments_for_long_columns():
-    """The planner's own choice for 1024 x 8192 (the cluster form would need
-    clusters of 8) is the y sweep without clusters, and it matches the
-    oracle over a few steps with graph replay."""
-    nx, ny, steps = 1024, 8192, 6
-    m, phi, tau, src, wav = _problem(nx, ny, steps, seed=5)
-    g = gpu_run(m, phi, tau, steps, src=src, wavelet=wav)
-    assert g["tuning"]["y_stage"] == 4, g["tuning"]
+    assert g["tuning"]["cols_per_cta"] == W
     o = oracle_run(m, phi, tau, steps, src=src, wavelet=wav)
     assert rel_l2(g["u_cur"], o["u_cur"]) < TOL
     assert rel_l2(g["u_prev"], o["u_prev"]) < TOL
