@@ -237,15 +237,21 @@ const char *adi_wave_last_error(const adi_wave *h);
  *                   and stores its own chunk) or ADI_STAGE_TMA (persistent
  *                   CTAs; the next rows of u^k and m arrive in shared memory
  *                   by TMA tensor copies while the current rows are solved;
- *                   FP32 tree solver, rows of >= 256 floats); FP64
- *                   elimination always reads directly;
- * x_cluster:        ADI_STAGE_TMA only: 1 = one CTA per row, 2 or 4 = each
- *                   row split over a cluster of that many CTAs (K = 32, one
- *                   row per cluster; 4: CTAs of 32..128 threads, four per
- *                   SM).
+ *                   FP32 tree solver, rows of >= 256 floats) or
+ *                   ADI_STAGE_BAND (each cluster of x_cluster = 2, 4 or 8
+ *                   CTAs walks a band of consecutive rows, keeping rows
+ *                   j - 1, j, j + 1 of u^k in shared memory: the halo rows
+ *                   come from there and every row is read from HBM once;
+ *                   K = 32, rows of at least 1024 unknowns per CTA);
+ *                   FP64 elimination always reads directly;
+ * x_cluster:        ADI_STAGE_TMA: 1 = one CTA per row, 2 or 4 = each row
+ *                   split over a cluster of that many CTAs (K = 32, one row
+ *                   per cluster; 4: CTAs of 32..128 threads, four per SM);
+ *                   ADI_STAGE_BAND: 2, 4 or 8 CTAs per row.
  * Zero fields mean "choose automatically". */
 enum { ADI_STAGE_AUTO = 0, ADI_STAGE_SMEM = 1, ADI_STAGE_L2 = 2, ADI_STAGE_DIRECT = 2,
-       ADI_STAGE_TMA = 3, ADI_STAGE_COOP = 4 /* y_stage only */ };
+       ADI_STAGE_TMA = 3, ADI_STAGE_COOP = 4 /* y_stage only */,
+       ADI_STAGE_BAND = 5 /* x_stage only */ };
 enum { ADI_SOLVER_AUTO = 0, ADI_SOLVER_TREE = 1, ADI_SOLVER_CR_SMEM = 2 };
 typedef struct {
     int32_t chunk_x, chunk_y;
@@ -279,14 +285,15 @@ int adi_wave_profile_read(adi_wave *h, double *ms, int64_t *launches,
                           int32_t n_kinds);
 
 /* ---- batched form (n_shots > 1) -------------------------------------------
- * mode 0 (default): every step of all shots is one persistent kernel launch
- * that hands out x-sweep and y-sweep work items of all shots from a global
- * queue (y items of a shot wait, bounded, for that shot's x items);
- * mode 1: the plain x and y kernels launched once per shot and step (the
- * comparison point);
- * mode 2: the same plain kernels, each shot's steps a chain on one of eight
- * streams that fork from and join into the caller's stream (parallel graph
- * branches when replayed), so shots overlap one another's launches and tails.
+ * mode 0: every step of all shots is one persistent kernel launch that hands
+ * out x-sweep and y-sweep work items of all shots from a global queue (y
+ * items of a shot wait, bounded, for that shot's x items);
+ * mode 1: the plain single-grid kernels (TMA-pipelined where the shape
+ * allows) launched once per shot and step, one after the other;
+ * mode 2 (default): the same plain kernels, each shot's steps a chain on one
+ * of eight streams that fork from and join into the caller's stream
+ * (parallel graph branches when replayed), so shots overlap one another's
+ * launches and tails.
  * ADI_EINVAL for other modes or single-grid handles. */
 int adi_wave_set_batch_mode(adi_wave *h, int32_t mode);
 

@@ -97,7 +97,7 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
       if (spc * tsys > maxT) spc = maxT / tsys;
     }
     if (x_smem_bytes(spc, tsys, P.fp64x, P.tree) > (size_t)kMaxDynSmem) { why = "x sweep shared memory too large"; return ADI_EUNSUPPORTED; }
-    if (t.x_stage < ADI_STAGE_AUTO || t.x_stage > ADI_STAGE_TMA) { why = "unknown x_stage"; return ADI_EINVAL; }
+    if (t.x_stage < ADI_STAGE_AUTO || t.x_stage > ADI_STAGE_BAND || t.x_stage == ADI_STAGE_COOP) { why = "unknown x_stage"; return ADI_EINVAL; }
     // TMA pipeline: FP32 tree solver, rows of >= 256 staged floats, K >= 8,
     // K = 32 only up to 512 threads (register budget)
     const bool pipe_ok = !P.fp64x && P.tree && tsys * K >= 256 && K >= 8 &&
@@ -110,11 +110,32 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
     // four CTAs of at least one warp each (four per SM)
     const bool quad_ok = pipe_ok && K == 32 && spc == 1 && tsys >= 128 && tsys <= 512 &&
                          x_pipe_smem_bytes(1, tsys / 4, K, 4) <= (size_t)kMaxDynSmem;
-    if (t.x_cluster < 0 || t.x_cluster > 4 || t.x_cluster == 3) { why = "x_cluster must be 0, 1, 2 or 4"; return ADI_EINVAL; }
+    if (t.x_cluster < 0 || t.x_cluster > 8 || (t.x_cluster > 2 && t.x_cluster != 4 && t.x_cluster != 8)) { why = "x_cluster must be 0, 1, 2, 4 or 8"; return ADI_EINVAL; }
+    // band form: rows of K = 32 split over 2, 4 or 8 CTAs of >= 32 threads
+    // each holding >= 1024 unknowns of the row
+    auto band_ok = [&](int xc) {
+      return !P.fp64x && P.tree && K == 32 && spc == 1 && tsys / xc >= 32 && tsys / xc <= 256 &&
+             xc * (tsys / xc / 32) <= 32 && x_band_smem_bytes(tsys / xc, K, xc) <= (size_t)kMaxDynSmem;
+    };
     const bool smem_ok = !P.fp64x &&
                          align64(x_smem_bytes(spc, tsys, P.fp64x, P.tree)) + x_stage_bytes(spc * tsys, K) <=
                              (size_t)kMaxDynSmem;
     int xs = t.x_stage;
+    // automatic: the band form over CTA pairs for rows of 256 or more
+    // threads at K = 32 (8192 columns and beyond; at 16384^2 0.856 against
+    // 0.942 ms for the row-block pipeline)
+    if (xs == ADI_STAGE_AUTO && (t.x_cluster == 0 || t.x_cluster == 2) && tsys >= 256 && band_ok(2))
+      xs = ADI_STAGE_BAND;
+    if (xs == ADI_STAGE_BAND) {
+      const int bxc = t.x_cluster >= 2 ? t.x_cluster : 2;
+      if (!band_ok(bxc)) { why = "x band form not available for this shape"; return ADI_EUNSUPPORTED; }
+      P.x_stage = xs;
+      P.xc = bxc;
+      P.kx = K;
+      P.log2tsys = ilog2(tsys);
+      P.spc = spc;
+      goto x_done;
+    }
     if (xs == ADI_STAGE_AUTO) xs = pipe_ok ? ADI_STAGE_TMA : ADI_STAGE_DIRECT;
     if (xs == ADI_STAGE_TMA && !pipe_ok) { why = "x TMA pipeline not available for this shape"; return ADI_EUNSUPPORTED; }
     if (xs == ADI_STAGE_SMEM && !smem_ok) {
@@ -139,6 +160,7 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
     P.log2tsys = ilog2(tsys);
     P.spc = spc;
   }
+x_done:
   // ---- y sweep
   {
     const int maxT = std::min(P.fp64y ? 512 : 1024, cty ? cty : 1024);

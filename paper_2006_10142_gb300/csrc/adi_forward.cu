@@ -31,7 +31,7 @@ namespace adi {
 // MAXT bounds the CTA size: 1024 caps a thread at 64 registers, 512 at 128,
 // 256 at 128 with two CTAs per SM; the launchers pick the smallest bound that
 // holds the CTA, so long chunks (K = 16, 32) keep their registers.
-constexpr int min_ctas(int maxt) { return maxt <= 128 ? 4 : maxt <= 256 ? 2 : 1; }
+constexpr int min_ctas(int maxt) { return maxt <= 64 ? 8 : maxt <= 128 ? 4 : maxt <= 256 ? 2 : 1; }
 
 template <int K, typename T, int MAXT, bool TREE>
 __global__ void __launch_bounds__(MAXT, min_ctas(MAXT)) x_sweep_kernel(const XArgs a) {
@@ -284,6 +284,150 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
   }
   if (tid < 32) bulk_wait_all();
   if constexpr (XC > 1) cgx::this_cluster().sync();  // no CTA leaves while its shared memory may be written
+  if (timed_out && (tid & 31) == 0 && a.err) atomicOr(a.err, ERR_TIMEOUT);
+}
+
+// ---------------------------------------------------------------------------
+// pass 1, band form (FP32, tree solver, K = 32, rows split over a cluster of
+// XC CTAs): each cluster walks a band of consecutive rows from top to bottom
+// and keeps a ring of three rows of u^k in shared memory (rows j - 1, j,
+// j + 1 of the row being solved), so the halo rows of the RHS stencil come
+// from shared memory and every row of u^k and m is read from HBM once.  While
+// row j is solved, TMA brings row j + 2 of u^k into the ring slot row j - 1
+// has just freed, and row j + 1 of m; w goes back through a swizzled stage by
+// TMA stores.  Rows outside the grid arrive as zeros (the Dirichlet ring).
+// Shared memory: [XSplitSmem] [mbarrier at a.stage_off] [pad to 1024 B]
+// [u ring: 3 x rowf] [m: rowf] [w: rowf] floats, rowf = tsys * K.
+// ---------------------------------------------------------------------------
+template <int K, int MAXT, int XC>
+__global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
+    x_band_kernel(const XArgs a, const __grid_constant__ CUtensorMap tm_u,
+                  const __grid_constant__ CUtensorMap tm_m, const __grid_constant__ CUtensorMap tm_w) {
+  static_assert(K == 32 && XC > 1, "band form: K = 32, rows over a cluster");
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int rank = cluster_rank(XC);
+  const int tsys = 1 << a.log2tsys;        // threads of this CTA (one row part)
+  const int rowf = tsys * K;               // floats per staged row part (>= 1024)
+  const int coff = rank * rowf;            // first column of this CTA's part
+  const int lines = rowf >> 5;             // 128-byte lines per row part
+  const int L = lines < 256 ? lines : 256; // lines per TMA box
+  const int nchunk = lines / L;
+  const uint32_t rowb = (uint32_t)(rowf * 4);
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  const uint32_t bar = sa + (uint32_t)a.stage_off;
+  const uint32_t st_u = (bar + 8u + 1023u) & ~1023u;  // ring slots 0, 1, 2
+  const uint32_t st_m = st_u + 3u * rowb;
+  const uint32_t st_w = st_m + rowb;
+  const float* su = reinterpret_cast<const float*>(smem + (st_u - sa));
+  const float* sm = reinterpret_cast<const float*>(smem + (st_m - sa));
+  float4* sw4 = reinterpret_cast<float4*>(smem + (st_w - sa));
+  const int nclu = (int)gridDim.x / XC;
+  const int band = (a.ny + nclu - 1) / nclu;
+  const int jb = ((int)blockIdx.x / XC) * band;
+  const int je = min(a.ny, jb + band);
+
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  // warp 0: copies of one row part of u^k into ring slot `slot` and/or of m
+  auto load_u = [&](int j, int slot) {
+    for (int c = lane; c < nchunk; c += 32)
+      tma_load_3d(st_u + (uint32_t)slot * rowb + (uint32_t)(c * L * 128), &tm_u, 0, c * L + rank * lines, j, bar);
+  };
+  auto load_m = [&](int j) {
+    for (int c = lane; c < nchunk; c += 32)
+      tma_load_3d(st_m + (uint32_t)(c * L * 128), &tm_m, 0, c * L + rank * lines, j, bar);
+  };
+  if (tid < 32 && jb < je) {
+    if (lane == 0) mbar_arrive_expect_tx(bar, 4u * rowb);
+    __syncwarp();
+    load_u(jb - 1, 0);
+    load_u(jb, 1);
+    load_u(jb + 1, 2);
+    load_m(jb);
+  }
+  const int li0 = tid * K;          // first unknown of this thread within the part
+  const int i0 = coff + li0;        // ... and within the row
+  uint32_t phase = 0;
+  bool timed_out = false;
+  for (int j = jb; j < je; ++j) {
+    const int r = j - jb;
+    const int sp = r % 3, sc = (r + 1) % 3, sn = (r + 2) % 3;  // ring slots of rows j - 1, j, j + 1
+    cluster_arrive_early(XC);
+    if (!mbar_wait_bounded(bar, phase, 1000000000ull)) timed_out = true;
+    phase ^= 1u;
+    const bool active = i0 < a.nx;
+    float d[K], s[K];
+    if (active) {
+      const float cx = (float)a.cx, cy = (float)a.cy, scf = (float)a.sc;
+      const float* up = su + (size_t)sp * rowf;
+      const float* uc_row = su + (size_t)sc * rowf;
+      const float* un = su + (size_t)sn * rowf;
+      float uc[K], v[K];
+      stage_vec<K>(d, up, li0);
+      stage_vec<K>(v, un, li0);
+#pragma unroll
+      for (int k = 0; k < K; ++k) d[k] += v[k];
+      stage_vec<K>(uc, uc_row, li0);
+      stage_vec<K>(v, sm, li0);
+      // neighbours across the split between the CTAs of a cluster come from L2
+      const size_t rowg = (size_t)j * a.ld;
+      const float uL = (i0 > 0) ? (li0 > 0 ? stage_at(uc_row, li0 - 1) : __ldg(a.u + rowg + i0 - 1)) : 0.f;
+      const float uR = (i0 + K < a.nx) ? (li0 + K < rowf ? stage_at(uc_row, li0 + K) : __ldg(a.u + rowg + i0 + K)) : 0.f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const float c = uc[k];
+        const float l = k > 0 ? uc[k - 1] : uL;
+        const float rr = k < K - 1 ? uc[k + 1] : uR;
+        const float lap = cx * (l + rr - 2.f * c) + cy * (d[k] - 2.f * c);
+        d[k] = v[k] * lap;
+        s[k] = scf * v[k];
+      }
+      // point source f^k = w(t_k) / (h1 h2) at one node
+      const GridDev* gd = a.gd;
+      const int sx = gd->src_ix;
+      if (j == gd->src_iy && sx >= i0 && sx < i0 + K) {
+        const long long lev = gd->k;
+        if (gd->wavelet != nullptr && lev >= 0 && lev < gd->n_wavelet) {
+          const float f = (float)a.src_scale * gd->wavelet[lev];
+#pragma unroll
+          for (int k = 0; k < K; ++k)
+            if (i0 + k == sx) d[k] += f;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < K; ++k) { d[k] = 0.f; s[k] = 0.f; }
+    }
+    if (tid < 32) bulk_wait_read();  // the previous row's w stage has been read out
+    __syncthreads();                 // slot of row j - 1 and the m stage are consumed
+    if (tid < 32 && j + 1 < je) {
+      fence_proxy_async_smem();
+      if (lane == 0) mbar_arrive_expect_tx(bar, 2u * rowb);
+      __syncwarp();
+      load_u(j + 2, sp);
+      load_m(j + 1);
+    }
+    x_solve_row_split<K, XC>(smem, rank, d, s);
+    // w through the swizzled stage, stored by TMA boxes
+#pragma unroll
+    for (int c = 0; c < K / 4; ++c)
+      sw4[swz4(li0 / 4 + c)] = make_float4(d[4 * c + 0], d[4 * c + 1], d[4 * c + 2], d[4 * c + 3]);
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid < 32) {
+      for (int c = lane; c < nchunk; c += 32)
+        if ((c * L + rank * lines) * 32 < a.ld)  // boxes past the pitch are not stored
+          tma_store_3d(&tm_w, 0, c * L + rank * lines, j, st_w + (uint32_t)(c * L * 128));
+      bulk_commit();
+    }
+  }
+  if (tid < 32) bulk_wait_all();
+  cgx::this_cluster().sync();  // no CTA leaves while its shared memory may be written
   if (timed_out && (tid & 31) == 0 && a.err) atomicOr(a.err, ERR_TIMEOUT);
 }
 
@@ -750,6 +894,52 @@ static cudaError_t launch_x_pipe_t(const XArgs& a_in, const CUtensorMap& tu, con
   return cudaLaunchKernelEx(&cfg, x_pipe_kernel<K, MAXT, XC>, a, tu, tm, tw);
 }
 
+// Band form: [XSplitSmem] [mbarrier] [pad to 1024] [u ring 3 x rowf] [m rowf] [w rowf].
+size_t x_band_smem_bytes(int tsys, int K, int xc) {
+  return align64(XSplitSmem::bytes(std::max(1, tsys / 32), xc)) + 8 + 1024 + (size_t)5 * tsys * K * 4;
+}
+
+template <int K, int MAXT, int XC>
+static cudaError_t launch_x_band_t(const XArgs& a_in, const CUtensorMap& tu, const CUtensorMap& tm,
+                                   const CUtensorMap& tw, cudaStream_t st) {
+  XArgs a = a_in;
+  const int l2 = XC == 2 ? 1 : XC == 4 ? 2 : 3;
+  if (a.spc != 1 || a.log2tsys < 5 + l2) return cudaErrorInvalidValue;
+  a.log2tsys -= l2;                      // threads of one CTA (one row part)
+  const int tsys = 1 << a.log2tsys;
+  if (tsys > MAXT || tsys % 32 != 0 || tsys * K < 1024) return cudaErrorInvalidValue;
+  if ((XC << a.log2tsys) / 32 > 32) return cudaErrorInvalidValue;  // top system of one warp
+  a.stage_off = (int)align64(XSplitSmem::bytes(std::max(1, tsys / 32), XC));
+  const size_t sm = x_band_smem_bytes(tsys, K, XC);
+  if (sm > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(a.ny * XC, 1, 1);
+  cfg.blockDim = dim3(tsys, 1, 1);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = XC;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nc = 0;
+  cudaError_t e = cudaOccupancyMaxActiveClusters(&nc, x_band_kernel<K, MAXT, XC>, &cfg);
+  if (e != cudaSuccess) return e;
+  cfg.gridDim = dim3(std::max(1, std::min(a.ny, nc)) * XC, 1, 1);
+  return cudaLaunchKernelEx(&cfg, x_band_kernel<K, MAXT, XC>, a, tu, tm, tw);
+}
+
+cudaError_t launch_x_band(const XArgs& a, int K, const CUtensorMap& tu, const CUtensorMap& tm,
+                          const CUtensorMap& tw, cudaStream_t st) {
+  if (K != 32) return cudaErrorInvalidValue;
+  if (a.xc == 2) return launch_x_band_t<32, 256, 2>(a, tu, tm, tw, st);
+  if (a.xc == 4) return launch_x_band_t<32, 128, 4>(a, tu, tm, tw, st);
+  if (a.xc == 8) return launch_x_band_t<32, 64, 8>(a, tu, tm, tw, st);
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_x_pipe(const XArgs& a, int K, const CUtensorMap& tu, const CUtensorMap& tm,
                           const CUtensorMap& tw, cudaStream_t st) {
   const int threads = a.spc << a.log2tsys;
@@ -955,6 +1145,9 @@ cudaError_t configure_kernels() {
   if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<32, 512, 1>, false);
   if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<32, 256, 2>, true);
   if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<32, 128, 4>, true);
+  if (e == cudaSuccess) e = allow_smem(x_band_kernel<32, 256, 2>, true);
+  if (e == cudaSuccess) e = allow_smem(x_band_kernel<32, 128, 4>, true);
+  if (e == cudaSuccess) e = allow_smem(x_band_kernel<32, 64, 8>, true);
   return e;
 }
 

@@ -152,6 +152,11 @@ cudaError_t configure_model_kernels();
 cudaError_t encode_row_map(CUtensorMap* out, const float* base, int ld, int ny, int box_lines);
 cudaError_t launch_x_pipe(const XArgs& a, int K, const CUtensorMap& tu, const CUtensorMap& tm,
                           const CUtensorMap& tw, cudaStream_t st);
+// Band form of the x sweep (x_stage 5): clusters of xc = 2, 4 or 8 CTAs walk
+// bands of consecutive rows with a ring of three rows of u^k in shared memory.
+size_t x_band_smem_bytes(int tsys, int K, int xc);
+cudaError_t launch_x_band(const XArgs& a, int K, const CUtensorMap& tu, const CUtensorMap& tm,
+                          const CUtensorMap& tw, cudaStream_t st);
 constexpr int kMaxDynSmem = 227 * 1024;
 cudaError_t configure_kernels();
 // Kernel attributes of every kernel of the library on the current device,

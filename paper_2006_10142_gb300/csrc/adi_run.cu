@@ -359,7 +359,7 @@ int adi_wave::launch_fwd(Grid& G, const float* u_cur, float* u_prev, float* w, f
 
   cudaEvent_t a = nullptr;
   if (profile && prof_begin(st, &a) != ADI_OK) return ADI_ECUDA;
-  if (P.x_stage == 3) {
+  if (P.x_stage == 3 || P.x_stage == 5) {
     const int L = x_pipe_box_lines((1 << P.log2tsys) / P.xc, P.kx);
     if (G.tm_lines != L) {
       CK(encode_row_map(&G.tm_buf[0], G.buf[0], G.ld, G.ny, L), "tensor map u0");
@@ -379,7 +379,8 @@ int adi_wave::launch_fwd(Grid& G, const float* u_cur, float* u_prev, float* w, f
       CK(encode_row_map(&tmpw, w, G.ld, G.ny, L), "tensor map w");
       tw = &tmpw;
     }
-    CK(launch_x_pipe(xa, P.kx, *tu, G.tm_m, *tw, st), "x sweep launch");
+    if (P.x_stage == 5) CK(launch_x_band(xa, P.kx, *tu, G.tm_m, *tw, st), "x sweep launch");
+    else CK(launch_x_pipe(xa, P.kx, *tu, G.tm_m, *tw, st), "x sweep launch");
   } else {
     CK(launch_x(xa, P.kx, P.fp64x, P.tree, st), "x sweep launch");
   }

@@ -132,8 +132,8 @@ struct adi_wave {
 
   // batched form (n_shots > 1)
   bool batch_fp64 = false;
-  int batch_mode = 0;                 // 0: persistent kernel, 1: plain kernels per shot,
-                                      // 2: plain kernels per shot on parallel branches
+  int batch_mode = 2;                 // 0: persistent kernel, 1: plain kernels per shot,
+                                      // 2 (default): plain kernels per shot on parallel branches
   static constexpr int kBranches = 8; // streams of batch mode 2
   cudaStream_t branch[kBranches] = {};
   cudaEvent_t fork_ev = nullptr;

@@ -21,9 +21,10 @@
 //     parallel cyclic reduction of 2C equations), so one round trip through
 //     L2 per item suffices, and unwinds its own segment;
 //   - the TMA pipeline of y_pipe_kernel is kept: the next item's w and m
-//     tiles stream into shared memory while the current item is solved; the
-//     current item's u^k, u^{k-1} boxes are prefetched into L2 when its
-//     solve starts.
+//     tiles stream into shared memory while the current item is solved, and
+//     its u^k, u^{k-1} boxes are prefetched into L2 once the current item's
+//     strip is complete (prefetched a whole item ahead, a part was evicted
+//     before use: 19.9 read bytes per point against 16).
 // Every wait ends: a CTA waits only for the items of its own strip, and the
 // lowest-numbered waiting item's missing strip-mates are either running or
 // queued behind lower-numbered items on resident CTAs that do not wait for
@@ -121,9 +122,9 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 2 : 1)
       else tma_load_2d(st_m + off, &tm_m, strip * W, row0 + b * BH, bar);
     }
   };
-  // warp 0: L2 prefetch of the u^k and u^{k-1} boxes item `it` updates --
-  // issued when the item's solve starts, so that they arrive during the
-  // solve and the wait for the strip and are not evicted before the update
+  // warp 0: L2 prefetch of the u^k and u^{k-1} boxes item `it` updates
+  // (issued for the next item once the current one's strip is complete,
+  // about half an item ahead of the update that reads them)
   auto prefetch_u = [&](int it) {
     const int strip = it / C, seg = it - (it / C) * C;
     const int row0 = seg * R;
@@ -190,6 +191,12 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 2 : 1)
         s[g + r] = colok ? sc * vm[r] : 0.f;
       }
     }
+    __syncthreads();  // the stage is consumed: refill it with the next item
+    const int next = item + (int)gridDim.x;
+    if (tid < 32 && next < nitems) {
+      fence_proxy_async_smem();
+      issue(next);
+    }
     // 1. partition: each thread's K rows to a two-equation summary
     Node<float> ndc;
     {
@@ -197,15 +204,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 2 : 1)
       chunk_reduce_split<K, float>(d, s, S, ndc);
       csum[col * tcol + q] = S;
     }
-    __syncthreads();  // the summaries are in place and the stage is consumed: refill it
-    const int next = item + (int)gridDim.x;
-    if (tid < 32) {
-      if (!ADJ) prefetch_u(item);
-      if (next < nitems) {
-        fence_proxy_async_smem();
-        issue(next);
-      }
-    }
+    __syncthreads();
     // 2. the segment of each column to one summary (tree over its chunks),
     // to global memory; the lane that stores a column's summary arrives on
     // the strip's counter with release semantics (its own store first), so
@@ -235,6 +234,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 2 : 1)
       }
     }
     __syncthreads();
+    if (!ADJ && tid < 32 && next < nitems) prefetch_u(next);
     // 3. the top systems of all W columns of the strip, one warp per column
     for (int c = warp; c < W; c += nwarps) {
       Eq<float> E0 = eq_identity<float>(), E1 = eq_identity<float>();
