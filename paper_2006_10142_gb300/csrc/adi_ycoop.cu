@@ -74,8 +74,10 @@ __host__ __device__ inline YCoopLayout y_coop_layout(int W, int tcol, int K, int
   return L;
 }
 
+// K = 16 (and CTAs of 256 threads) run two CTAs per SM (64 registers per
+// thread at 512 threads); K = 32 with 512 threads one.
 template <int K, int MAXT, int W, bool ADJ>
-__global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 2 : 1)
+__global__ void __launch_bounds__(MAXT, (MAXT <= 256 || K == 16) ? 2 : 1)
     y_coop_kernel(const YArgs a, const YCoop yc, const __grid_constant__ CUtensorMap tm_w,
                   const __grid_constant__ CUtensorMap tm_m, const __grid_constant__ CUtensorMap tm_uc,
                   const __grid_constant__ CUtensorMap tm_up) {
