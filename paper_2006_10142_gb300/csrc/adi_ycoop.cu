@@ -255,12 +255,10 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 || K == 16) ? 2 : 1)
     __syncthreads();
     // every read of this strip's summaries and counter is done: the last CTA
     // of the strip resets its counters for the next launch
-    if (tid == 0) {
-      if (atomicAdd(yc.sync + 2 * strip + 1, 1) == C - 1) {
-        yc.sync[2 * strip] = 0;
-        yc.sync[2 * strip + 1] = 0;
-      }
-    }
+    // completion count of the strip (its reply is first needed after the
+    // update, so the round trip overlaps the rest of the item)
+    int done_before = 0;
+    if (tid == 0) done_before = atomicAdd(yc.sync + 2 * strip + 1, 1);
     // 4. down the column trees to each chunk's end values, back substitution
     {
       float xa = xtop[2 * (tc * C + seg)];
@@ -322,6 +320,12 @@ __global__ void __launch_bounds__(MAXT, (MAXT <= 256 || K == 16) ? 2 : 1)
       bad |= chk != 0.f;
     }
     if (!ADJ && item == 0 && tid == 0 && a.gd) a.gd->k += 1;
+    // every CTA of the strip has read its summaries and counter: the last
+    // one resets the counters for the next launch
+    if (tid == 0 && done_before == C - 1) {
+      yc.sync[2 * strip] = 0;
+      yc.sync[2 * strip + 1] = 0;
+    }
     __syncthreads();  // csum and xtop are reused by the next item
   }
   if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0 && a.err) atomicOr(a.err, ERR_NUMERIC);

@@ -97,6 +97,7 @@ def test_dependency_wait_times_out_without_fault():
     t = lambda a: torch.from_numpy(f32(a)).to(dev)
     B = api.AdiWaveBatch([t(s["m"]) for s in shots], [t(s["phi"]) for s in shots],
                          [s["tau"] for s in shots])
+    B.set_mode(0)  # the persistent kernel's dependency wait
     B.set_wait_hook(spin_limit=2000, never_ready_shot=1)
     B.run(1)
     with pytest.raises(api.AdiError) as ei:
@@ -113,8 +114,9 @@ def test_dependency_wait_times_out_without_fault():
 
 @pytest.mark.slow
 def test_batch_64_shots_workload():
-    """64 shots with n drawn from {256, 512, 1024, 2048}, 500 steps; two shots
-    checked against the oracle's full run."""
+    """64 shots with n drawn from {256, 512, 1024, 2048}, 500 steps, in the
+    default batch mode; three shots (256, 1024, 2048) checked against the
+    oracle's full run."""
     import torch
     from paper_2006_10142_gb300 import api
     sizes = inputs.batch_sizes(64, seed=0)
@@ -125,7 +127,7 @@ def test_batch_64_shots_workload():
     B = api.AdiWaveBatch([t(p.m) for p in probs], [t(p.phi) for p in probs], [p.tau for p in probs])
     B.run(steps, srcs=[p.src for p in probs], wavelets=[t(p.wavelet) for p in probs])
     B.sync_status()
-    picks = [sizes.index(256), sizes.index(1024)]
+    picks = [sizes.index(256), sizes.index(1024), sizes.index(2048)]
     for b in picks:
         p = probs[b]
         _, uc, k = B.state(b)
