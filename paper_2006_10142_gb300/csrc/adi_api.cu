@@ -111,10 +111,11 @@ int plan_grid(Grid& G, const adi_wave_tuning& t, std::string& why) {
     const bool quad_ok = pipe_ok && K == 32 && spc == 1 && tsys >= 128 && tsys <= 512 &&
                          x_pipe_smem_bytes(1, tsys / 4, K, 4) <= (size_t)kMaxDynSmem;
     if (t.x_cluster < 0 || t.x_cluster > 8 || (t.x_cluster > 2 && t.x_cluster != 4 && t.x_cluster != 8)) { why = "x_cluster must be 0, 1, 2, 4 or 8"; return ADI_EINVAL; }
-    // band form: rows of K = 32 split over 2, 4 or 8 CTAs of >= 32 threads
-    // each holding >= 1024 unknowns of the row
+    // band form: rows of K = 16 or 32 split over 2, 4 or 8 CTAs of >= 32
+    // threads (at most 512 / 256) each holding >= 1024 unknowns of the row
     auto band_ok = [&](int xc) {
-      return !P.fp64x && P.tree && K == 32 && spc == 1 && tsys / xc >= 32 && tsys / xc <= 256 &&
+      return !P.fp64x && P.tree && (K == 16 || K == 32) && spc == 1 && tsys / xc >= 32 &&
+             tsys / xc <= (K == 16 ? 512 : 256) && tsys / xc * K >= 1024 &&
              xc * (tsys / xc / 32) <= 32 && x_band_smem_bytes(tsys / xc, K, xc) <= (size_t)kMaxDynSmem;
     };
     const bool smem_ok = !P.fp64x &&

@@ -288,8 +288,8 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
 }
 
 // ---------------------------------------------------------------------------
-// pass 1, band form (FP32, tree solver, K = 32, rows split over a cluster of
-// XC CTAs): each cluster walks a band of consecutive rows from top to bottom
+// pass 1, band form (FP32, tree solver, K = 16 or 32, rows split over a
+// cluster of XC CTAs): each cluster walks a band of consecutive rows from top to bottom
 // and keeps a ring of three rows of u^k in shared memory (rows j - 1, j,
 // j + 1 of the row being solved), so the halo rows of the RHS stencil come
 // from shared memory and every row of u^k and m is read from HBM once.  While
@@ -303,7 +303,7 @@ template <int K, int MAXT, int XC>
 __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
     x_band_kernel(const XArgs a, const __grid_constant__ CUtensorMap tm_u,
                   const __grid_constant__ CUtensorMap tm_m, const __grid_constant__ CUtensorMap tm_w) {
-  static_assert(K == 32 && XC > 1, "band form: K = 32, rows over a cluster");
+  static_assert((K == 16 || K == 32) && XC > 1, "band form: K = 16 or 32, rows over a cluster");
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -933,10 +933,15 @@ static cudaError_t launch_x_band_t(const XArgs& a_in, const CUtensorMap& tu, con
 
 cudaError_t launch_x_band(const XArgs& a, int K, const CUtensorMap& tu, const CUtensorMap& tm,
                           const CUtensorMap& tw, cudaStream_t st) {
-  if (K != 32) return cudaErrorInvalidValue;
-  if (a.xc == 2) return launch_x_band_t<32, 256, 2>(a, tu, tm, tw, st);
-  if (a.xc == 4) return launch_x_band_t<32, 128, 4>(a, tu, tm, tw, st);
-  if (a.xc == 8) return launch_x_band_t<32, 64, 8>(a, tu, tm, tw, st);
+  if (K == 32) {
+    if (a.xc == 2) return launch_x_band_t<32, 256, 2>(a, tu, tm, tw, st);
+    if (a.xc == 4) return launch_x_band_t<32, 128, 4>(a, tu, tm, tw, st);
+    if (a.xc == 8) return launch_x_band_t<32, 64, 8>(a, tu, tm, tw, st);
+  } else if (K == 16) {
+    if (a.xc == 2) return launch_x_band_t<16, 512, 2>(a, tu, tm, tw, st);
+    if (a.xc == 4) return launch_x_band_t<16, 256, 4>(a, tu, tm, tw, st);
+    if (a.xc == 8) return launch_x_band_t<16, 128, 8>(a, tu, tm, tw, st);
+  }
   return cudaErrorInvalidValue;
 }
 
@@ -1148,6 +1153,9 @@ cudaError_t configure_kernels() {
   if (e == cudaSuccess) e = allow_smem(x_band_kernel<32, 256, 2>, true);
   if (e == cudaSuccess) e = allow_smem(x_band_kernel<32, 128, 4>, true);
   if (e == cudaSuccess) e = allow_smem(x_band_kernel<32, 64, 8>, true);
+  if (e == cudaSuccess) e = allow_smem(x_band_kernel<16, 512, 2>, true);
+  if (e == cudaSuccess) e = allow_smem(x_band_kernel<16, 256, 4>, true);
+  if (e == cudaSuccess) e = allow_smem(x_band_kernel<16, 128, 8>, true);
   return e;
 }
 

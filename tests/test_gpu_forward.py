@@ -288,16 +288,17 @@ def test_y_segments_through_global_memory_match_oracle(nx, ny, W, ky, ty):
 @pytest.mark.parametrize("nx,ny", [(16384, 600), (12000, 33), (9000, 20), (4096, 300),
                                    (2500, 1000)])
 @pytest.mark.parametrize("xc", [2, 4, 8])
-def test_x_band_form_matches_oracle(nx, ny, xc):
+@pytest.mark.parametrize("kx", [32, 16])
+def test_x_band_form_matches_oracle(nx, ny, xc, kx):
     """The band form of the x sweep (x_stage 5): clusters of 2, 4 or 8 CTAs
     walk bands of consecutive rows with rows j - 1, j, j + 1 of u^k in a
     shared-memory ring; bands of one to many rows, the grid's first and last
     rows (zero halo rows from the copies' fill), cluster ranks partly or
-    wholly past the row."""
+    wholly past the row; 32 or 16 unknowns per thread."""
     from paper_2006_10142_gb300 import _lib
     steps = 4
     m, phi, tau, src, wav = _problem(nx, ny, steps, seed=nx % 89 + ny)
-    tun = dict(x_stage=5, chunk_x=32, x_cluster=xc, rows_per_cta=1)
+    tun = dict(x_stage=5, chunk_x=kx, x_cluster=xc, rows_per_cta=1)
     try:
         g = gpu_run(m, phi, tau, steps, src=src, wavelet=wav, tuning=tun)
     except _lib.AdiError as e:
