@@ -17,14 +17,14 @@ def test_roofline_takes_the_kernel_with_the_most_time():
     n = 16384
     kms = {0: 947.0, 1: 1443.0}        # total ms over the timed region
     kcnt = {0: 1000, 1: 1000}
-    kinds = {0: "x_pipe_kernel", 1: "y_pipe_kernel"}
+    kinds = {0: "x_band_kernel", 1: "y_coop_kernel"}
     alg = {0: 12 * n * n, 1: 20 * n * n}
     r = bench._roofline(kms, kcnt, kinds, alg, "ricker_16384")
-    assert r["kernel"] == "y_pipe_kernel" and r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["kernel"] == "y_coop_kernel" and r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert r["avg_launch_ms"] == pytest.approx(1.443)
     assert r["achieved"] == pytest.approx(20 * n * n / 1.443e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
-    assert r["traffic"] == bench.NCU_TRAFFIC[("ricker_16384", "y_pipe_kernel")]
+    assert r["traffic"] == bench.NCU_TRAFFIC[("ricker_16384", "y_coop_kernel")]
     peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")  # written per machine, not versioned
     if os.path.exists(peaks):
         with open(peaks) as f:
@@ -35,7 +35,7 @@ def test_roofline_takes_the_kernel_with_the_most_time():
     assert bench._roofline(kms, kcnt, kinds, alg, "ricker_4096")["traffic"] is None
     # the x sweep dominates when it takes longer
     r2 = bench._roofline({0: 2000.0, 1: 1000.0}, kcnt, kinds, alg)
-    assert r2["kernel"] == "x_pipe_kernel"
+    assert r2["kernel"] == "x_band_kernel"
     assert r2["achieved"] == pytest.approx(12 * n * n / 2.0e-3 / 1e9)
 
 
