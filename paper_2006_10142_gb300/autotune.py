@@ -23,7 +23,7 @@ import json
 import os
 from typing import Dict
 
-X_KNOBS = ("chunk_x", "rows_per_cta", "cta_threads", "x_stage")
+X_KNOBS = ("chunk_x", "rows_per_cta", "cta_threads", "x_stage", "x_cluster")
 Y_KNOBS = ("chunk_y", "cols_per_cta", "cta_threads_y", "y_stage")
 SHARED_KNOBS = ("solver", "pcr_size")
 
@@ -59,9 +59,12 @@ def candidates(nx: int, ny: int):
     shared = [dict(solver=1, pcr_size=0), dict(solver=2, pcr_size=8), dict(solver=2, pcr_size=32)]
     # stage 3 = the TMA-pipelined persistent sweeps, 2 = direct loads (x) or
     # L2 prefetch (y), 1 = shared-memory staging, 4 = (y only) persistent CTAs
-    # whose column segments meet through global memory
-    xs = [dict(chunk_x=k, rows_per_cta=0, cta_threads=t, x_stage=s)
+    # whose column segments meet through global memory, 5 = (x only) the band
+    # form, each row over a cluster of x_cluster CTAs
+    xs = [dict(chunk_x=k, rows_per_cta=0, cta_threads=t, x_stage=s, x_cluster=0)
           for k, t, s in itertools.product((8, 16, 32), (256, 512, 1024), (3, 2))]
+    xs += [dict(chunk_x=k, rows_per_cta=0, cta_threads=0, x_stage=5, x_cluster=c)
+           for k, c in itertools.product((32, 16), (2, 4))]
     ys = [dict(chunk_y=k, cols_per_cta=w, cta_threads_y=t, y_stage=s)
           for k, w, t, s in itertools.product((8, 16, 32), (8, 16), (256, 512, 1024), (4, 3, 1, 2))]
     return shared, xs, ys

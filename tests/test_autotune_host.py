@@ -58,7 +58,7 @@ def test_search_skips_rejected_shapes_and_can_find_nothing():
 
 def test_candidates_cover_every_stage_mode():
     shared, xs, ys = autotune.candidates(4096, 4096)
-    assert {c["x_stage"] for c in xs} == {2, 3}
+    assert {c["x_stage"] for c in xs} == {2, 3, 5}
     assert {c["y_stage"] for c in ys} == {1, 2, 3, 4}
     assert all(set(c) == set(autotune.X_KNOBS) for c in xs)
     assert all(set(c) == set(autotune.Y_KNOBS) for c in ys)
