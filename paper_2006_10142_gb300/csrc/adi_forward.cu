@@ -1284,9 +1284,31 @@ cudaError_t launch_init(int nx, int ny, int ld, const float* m_pitched, const fl
   return cudaGetLastError();
 }
 
+__global__ void scan_init_kernel(unsigned int* out3) {
+  out3[0] = 0x7f7fffffu;
+  out3[1] = 0u;
+  out3[2] = 0u;
+}
+
+__global__ void scan_out_kernel(const unsigned int* out3, volatile unsigned int* host3) {
+  host3[0] = out3[0];
+  host3[1] = out3[1];
+  host3[2] = out3[2];
+  __threadfence_system();
+}
+
 cudaError_t launch_scan_m(const float* m, int nx, int ny, int ld, unsigned int* out3,
-                          cudaStream_t st) {
+                          unsigned int* host3, cudaStream_t st) {
+  scan_init_kernel<<<1, 1, 0, st>>>(out3);
   scan_m_kernel<<<152 * 4, 256, 0, st>>>(m, nx, ny, ld, out3);
+  scan_out_kernel<<<1, 1, 0, st>>>(out3, host3);
+  return cudaGetLastError();
+}
+
+__global__ void put_gd_kernel(GridDev* dst, const GridDev v) { *dst = v; }
+
+cudaError_t launch_put_gd(GridDev* dst, const GridDev& v, cudaStream_t st) {
+  put_gd_kernel<<<1, 1, 0, st>>>(dst, v);
   return cudaGetLastError();
 }
 

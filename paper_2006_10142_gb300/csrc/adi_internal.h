@@ -72,8 +72,13 @@ cudaError_t launch_init(int nx, int ny, int ld, const float* m_pitched, const fl
                         const float* psi, float* u0, float* u1, double tau, double cx_half,
                         double cy_half, int taylor, int src_ix, int src_iy, double src_half,
                         const float* wavelet, int n_wavelet, cudaStream_t st);
+// min(m), max(m) bit patterns and a non-finite/non-positive flag into out3
+// (device) and then host3 (mapped pinned host memory, device address): three
+// launches, no copies.
 cudaError_t launch_scan_m(const float* m, int nx, int ny, int ld, unsigned int* out3,
-                          cudaStream_t st);
+                          unsigned int* host3, cudaStream_t st);
+// *dst = v on the stream (one-thread kernel; v travels as the argument).
+cudaError_t launch_put_gd(GridDev* dst, const GridDev& v, cudaStream_t st);
 size_t x_smem_bytes(int spc, int tsys, bool fp64, bool tree);
 size_t y_smem_bytes(int W, int C, int tcol, bool fp64, bool tree);
 size_t y_stage_bytes(int threads, int K);

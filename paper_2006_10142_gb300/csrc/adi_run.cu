@@ -82,8 +82,11 @@ int adi_wave::ensure_ycoop(Grid& G) {
   return ADI_OK;
 }
 
+// The grid record goes to the device as a kernel argument: no copy engine
+// and no host buffer that must outlive the call.
 int adi_wave::upload_gd(Grid& G, cudaStream_t st) {
-  CK(cudaMemcpyAsync(G.gd, &G.hgd, sizeof(GridDev), cudaMemcpyHostToDevice, st), "upload grid state");
+  CK(launch_put_gd(G.gd, G.hgd, st), "upload grid state");
+  launches += 1;
   return ADI_OK;
 }
 
@@ -210,13 +213,16 @@ int adi_wave::start_grid(int s, const float* m, const float* phi, const float* p
     CK(cudaMemcpy2DAsync(G.m, sizeof(float) * G.ld, m, sizeof(float) * G.nx,
                          sizeof(float) * G.nx, G.ny, cudaMemcpyDeviceToDevice, st), "copy m");
     if (!scan) CK(cudaMalloc(&scan, 3 * sizeof(unsigned int)), "alloc scan");
-    const unsigned int init3[3] = {0x7f7fffffu, 0u, 0u};
-    unsigned int res3[3];
-    CK(cudaMemcpyAsync(scan, init3, sizeof(init3), cudaMemcpyHostToDevice, st), "scan init");
-    CK(launch_scan_m(G.m, G.nx, G.ny, G.ld, scan, st), "scan m");
-    CK(cudaMemcpyAsync(res3, scan, sizeof(res3), cudaMemcpyDeviceToHost, st), "scan read");
+    if (!scan_host) {
+      unsigned int* hp = nullptr;
+      CK(cudaHostAlloc((void**)&hp, 4 * sizeof(unsigned int), cudaHostAllocMapped), "alloc scan result");
+      scan_host = hp;
+      CK(cudaHostGetDevicePointer((void**)&scan_host_dev, hp, 0), "map scan result");
+    }
+    CK(launch_scan_m(G.m, G.nx, G.ny, G.ld, scan, scan_host_dev, st), "scan m");
     CK(cudaStreamSynchronize(st), "scan sync");
-    launches += 1;
+    unsigned int res3[3] = {scan_host[0], scan_host[1], scan_host[2]};
+    launches += 3;
     if (res3[2]) return fail(this, ADI_EINVAL, "m must be finite and > 0 everywhere");
     float lo, hi;
     memcpy(&lo, &res3[0], 4);
@@ -664,6 +670,7 @@ adi_wave::~adi_wave() {
   for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
   if (d_err) cudaFree(d_err);
   if (scan) cudaFree(scan);
+  if (scan_host) cudaFreeHost(const_cast<unsigned int*>(scan_host));
   if (d_rec) cudaFree(d_rec);
   if (d_shots) cudaFree(d_shots);
   if (d_items) cudaFree(d_items);

@@ -116,6 +116,11 @@ struct adi_wave {
   int* d_err = nullptr;
   int* d_rec = nullptr;
   unsigned int* scan = nullptr;
+  // the scan's result, written by a kernel into mapped pinned host memory so
+  // that reading it needs no copy engine (those may be busy with a caller's
+  // large copies on other streams)
+  volatile unsigned int* scan_host = nullptr;
+  unsigned int* scan_host_dev = nullptr;
   int rec_cap = 0;
   cudaStream_t cap = nullptr;  // private stream used only for graph capture
   cudaGraphExec_t pair[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [orientation][gather]
