@@ -771,7 +771,13 @@ __global__ void init_kernel(int nx, int ny, int ld, const float* __restrict__ m,
   const int j = blockIdx.y;
   if (i >= nx || j >= ny) return;
   const size_t c = (size_t)j * nx + i;
-  const double ph = phi[c];
+  const float phf = phi[c];
+  if (!psi && !taylor) {  // u^1 = u^0 = phi: no arithmetic
+    u0[(size_t)j * ld + i] = phf;
+    u1[(size_t)j * ld + i] = phf;
+    return;
+  }
+  const double ph = phf;
   double v = ph + (psi ? tau * (double)psi[c] : 0.0);
   if (taylor) {
     const double l = (i > 0) ? phi[c - 1] : 0.0;
@@ -791,15 +797,17 @@ __global__ void init_kernel(int nx, int ny, int ld, const float* __restrict__ m,
 __global__ void scan_m_kernel(const float* __restrict__ m, int nx, int ny, int ld,
                               unsigned int* out3) {
   unsigned int lo = 0x7f7fffffu, hi = 0u, bad = 0u;
-  const size_t total = (size_t)nx * ny;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
-       t += (size_t)gridDim.x * blockDim.x) {
-    const size_t j = t / nx, i = t % nx;
-    const float v = m[j * ld + i];
-    if (!(v > 0.0f) || !isfinite(v)) { bad = 1u; continue; }
-    const unsigned int b = __float_as_uint(v);
-    lo = min(lo, b);
-    hi = max(hi, b);
+  // rows strided over the CTAs, columns over a CTA's threads (no division
+  // per element)
+  for (int j = blockIdx.x; j < ny; j += gridDim.x) {
+    const float* row = m + (size_t)j * ld;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const float v = row[i];
+      if (!(v > 0.0f) || !isfinite(v)) { bad = 1u; continue; }
+      const unsigned int b = __float_as_uint(v);
+      lo = min(lo, b);
+      hi = max(hi, b);
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
