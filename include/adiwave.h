@@ -116,7 +116,12 @@ int adi_wave_init(adi_wave **out, const adi_wave_desc *desc, int32_t n_shots,
 /* Re-run the start-up of Eq. (CN2) in place on an existing handle: copy new
  * coefficients m (may be NULL = keep), initial data phi (and psi, may be
  * NULL) of every shot, set the level back to k = 1 and forget the recorded
- * run.  Same pointer conventions as adi_wave_init; allocates nothing. */
+ * run.  Same pointer conventions as adi_wave_init.  A new m is scanned for
+ * its range first (the plan depends on it; the host waits for the scan):
+ * a coefficient that is not finite and > 0 gives ADI_EINVAL and leaves that
+ * shot's medium, plan and state unchanged.  Allocates nothing, except the
+ * y sweep's segment scratch the first time a new medium moves the plan to
+ * ADI_STAGE_COOP. */
 int adi_wave_reset(adi_wave *h, const float *const *m, const float *const *phi,
                    const float *const *psi, const adi_source *src, void *stream);
 

@@ -210,8 +210,8 @@ int adi_wave::start_grid(int s, const float* m, const float* phi, const float* p
                          const adi_source* sr, cudaStream_t st) {
   Grid& G = g[s];
   if (m) {
-    CK(cudaMemcpy2DAsync(G.m, sizeof(float) * G.ld, m, sizeof(float) * G.nx,
-                         sizeof(float) * G.nx, G.ny, cudaMemcpyDeviceToDevice, st), "copy m");
+    // the caller's medium is scanned before it replaces the handle's, so a
+    // rejected one leaves the handle as it was
     if (!scan) CK(cudaMalloc(&scan, 3 * sizeof(unsigned int)), "alloc scan");
     if (!scan_host) {
       unsigned int* hp = nullptr;
@@ -219,11 +219,13 @@ int adi_wave::start_grid(int s, const float* m, const float* phi, const float* p
       scan_host = hp;
       CK(cudaHostGetDevicePointer((void**)&scan_host_dev, hp, 0), "map scan result");
     }
-    CK(launch_scan_m(G.m, G.nx, G.ny, G.ld, scan, scan_host_dev, st), "scan m");
+    CK(launch_scan_m(m, G.nx, G.ny, G.nx, scan, scan_host_dev, st), "scan m");
     CK(cudaStreamSynchronize(st), "scan sync");
     unsigned int res3[3] = {scan_host[0], scan_host[1], scan_host[2]};
     launches += 3;
     if (res3[2]) return fail(this, ADI_EINVAL, "m must be finite and > 0 everywhere");
+    CK(cudaMemcpy2DAsync(G.m, sizeof(float) * G.ld, m, sizeof(float) * G.nx,
+                         sizeof(float) * G.nx, G.ny, cudaMemcpyDeviceToDevice, st), "copy m");
     float lo, hi;
     memcpy(&lo, &res3[0], 4);
     memcpy(&hi, &res3[1], 4);

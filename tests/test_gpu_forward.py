@@ -209,6 +209,39 @@ def test_non_finite_state_sets_numeric_flag():
     h.close()
 
 
+@pytest.mark.parametrize("bad", [0.0, -1.0, float("nan"), float("inf")])
+def test_medium_must_be_finite_and_positive(bad):
+    """The range scan of m (Eq. f1 needs c^2 > 0) rejects a zero, negative or
+    non-finite coefficient anywhere, at init and at a reset with a new
+    medium; a rejected reset leaves the handle's medium and state as they
+    were."""
+    import torch
+    from helpers import f32
+    from paper_2006_10142_gb300 import _lib, api
+    dev = torch.device("cuda:0")
+    nx, ny, steps = 70, 45, 5
+    m, phi, tau, src, wav = _problem(nx, ny, steps, seed=11)
+    m_d = torch.from_numpy(f32(m)).to(dev)
+    phi_d = torch.from_numpy(f32(phi)).to(dev)
+    mb = m_d.clone()
+    mb[ny // 2, nx - 1] = bad
+    with pytest.raises(_lib.AdiError) as ei:
+        api.AdiWave(mb, phi_d, tau)
+    assert ei.value.code == _lib.ADI_EINVAL
+    h = api.AdiWave(m_d, phi_d, tau)
+    with pytest.raises(_lib.AdiError) as ei:
+        h.reset(phi_d, m=mb)
+    assert ei.value.code == _lib.ADI_EINVAL
+    h.run(steps, src=src, wavelet=torch.from_numpy(f32(wav)).to(dev))
+    h.sync_status()
+    up, uc, k = h.state()
+    h.close()
+    o = oracle_run(m, phi, tau, steps, src=src, wavelet=wav)
+    assert k == steps + 1
+    assert rel_l2(uc.double().cpu().numpy(), o["u_cur"]) < TOL
+    assert rel_l2(up.double().cpu().numpy(), o["u_prev"]) < TOL
+
+
 def test_invalid_run_arguments():
     import torch
     from paper_2006_10142_gb300 import api
