@@ -145,10 +145,13 @@ int adi_wave::enqueue_batch_step(cudaStream_t st) {
 }
 
 // Batch mode 2: every shot's steps are a chain of the single-grid kernels on
-// one of kBranches streams (shot s on branch s mod kBranches); the branches
-// fork from `st` and join back into it, so shots of different sizes overlap
-// and fill each other's tails, with no barrier between shots inside the
-// `nsteps` steps.
+// one of kBranches streams; the branches fork from `st` and join back into
+// it, so shots of different sizes overlap and fill each other's tails, with
+// no barrier between shots inside the `nsteps` steps.  Shots go to branches
+// largest first, each to the branch with the fewest grid points so far, so
+// that the branches end together at the join (for 64 shots of 256^2 to
+// 2048^2 the fullest branch holds 1.004 of an even share, against 1.36 with
+// shot s on branch s mod kBranches); they are launched in that order too.
 int adi_wave::ensure_branches() {
   if (fork_ev) return ADI_OK;
   for (int b = 0; b < kBranches; ++b) {
@@ -164,11 +167,25 @@ int adi_wave::enqueue_batch_steps_parallel(int nsteps, cudaStream_t st) {
   if (rc != ADI_OK) return rc;
   const int n = (int)g.size();
   const int nb = std::min(n, (int)kBranches);
+  if ((int)shot_order.size() != n) {
+    shot_order.resize(n);
+    shot_branch.assign(n, 0);
+    for (int s = 0; s < n; ++s) shot_order[s] = s;
+    std::stable_sort(shot_order.begin(), shot_order.end(), [&](int a, int b) {
+      return (long long)g[a].nx * g[a].ny > (long long)g[b].nx * g[b].ny;
+    });
+    std::vector<long long> load(nb, 0);
+    for (int s : shot_order) {
+      const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      shot_branch[s] = b;
+      load[b] += (long long)g[s].nx * g[s].ny;
+    }
+  }
   CKB(cudaEventRecord(fork_ev, st), "fork");
   for (int b = 0; b < nb; ++b) CKB(cudaStreamWaitEvent(branch[b], fork_ev, 0), "branch wait");
-  for (int s = 0; s < n; ++s) {
+  for (int s : shot_order) {
     Grid& G = g[s];
-    cudaStream_t bs = branch[s % nb];
+    cudaStream_t bs = branch[shot_branch[s]];
     int cur = G.cur;
     for (int t = 0; t < nsteps; ++t) {
       rc = launch_fwd(G, G.buf[cur], G.buf[1 - cur], G.w, nullptr, G.gd, bs);

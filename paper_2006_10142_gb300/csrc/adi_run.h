@@ -143,6 +143,8 @@ struct adi_wave {
   cudaStream_t branch[kBranches] = {};
   cudaEvent_t fork_ev = nullptr;
   cudaEvent_t join_ev[kBranches] = {};
+  std::vector<int> shot_order;  // batch mode 2: shots by decreasing size
+  std::vector<int> shot_branch; // batch mode 2: branch of each shot
   int ensure_branches();
   int enqueue_batch_steps_parallel(int nsteps, cudaStream_t st);
   adi::BatchShot* d_shots = nullptr;
