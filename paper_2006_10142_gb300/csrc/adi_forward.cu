@@ -399,8 +399,12 @@ __device__ __forceinline__ void x_solve_row_async(unsigned char* smem, int rank,
 // The CTAs of a cluster exchange their warp summaries with st.async
 // (x_solve_row_async), so no cluster barrier runs per row (0.720 against
 // 0.855 ms per 16384^2 launch with the barrier-synchronised exchange).
+// The unknowns on either side of a CTA's part (the neighbouring CTAs'
+// columns) come with each ring row as two 16-byte bulk copies on the same
+// mbarrier, so the RHS never waits on a load from L2.
 // Shared memory: [XAsyncSmem] [mbarrier at a.stage_off] [pad to 1024 B]
-// [u ring: 3 x rowf] [m: rowf] [w: rowf] floats, rowf = tsys * K.
+// [u ring: 3 x rowf] [m: rowf] [w: rowf] floats, rowf = tsys * K,
+// [halo: 3 ring slots x (left, right) 16-byte groups].
 // ---------------------------------------------------------------------------
 template <int K, int MAXT, int XC>
 __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
@@ -426,6 +430,12 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
   const float* su = reinterpret_cast<const float*>(smem + (st_u - sa));
   const float* sm = reinterpret_cast<const float*>(smem + (st_m - sa));
   float4* sw4 = reinterpret_cast<float4*>(smem + (st_w - sa));
+  const uint32_t st_h = st_w + rowb;  // halo of ring slot s at st_h + 32 s: left, right group
+  const float* sh = reinterpret_cast<const float*>(smem + (st_h - sa));
+  // the left group [coff - 4, coff) exists for every rank but the first; the
+  // right group [coff + rowf, + 4) when a next rank's columns lie in the row
+  const bool has_l = rank > 0;
+  const bool has_r = rank + 1 < XC && (size_t)coff + rowf + 4 <= (size_t)a.ld;
   const int nclu = (int)gridDim.x / XC;
   const int band = (a.ny + nclu - 1) / nclu;
   const int jb = ((int)blockIdx.x / XC) * band;
@@ -449,13 +459,28 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
     for (int c = lane; c < nchunk; c += 32)
       tma_load_3d(st_m + (uint32_t)(c * L * 128), &tm_m, 0, c * L + rank * lines, j, bar);
   };
+  // lane 0: the halo groups of row j (rows outside the grid have none)
+  auto halo_bytes = [&](int j) -> uint32_t {
+    return (j >= 0 && j < a.ny) ? 16u * ((has_l ? 1u : 0u) + (has_r ? 1u : 0u)) : 0u;
+  };
+  auto load_halo = [&](int j, int slot) {
+    if (j < 0 || j >= a.ny) return;
+    const float* row = a.u + (size_t)j * a.ld;
+    if (has_l) bulk_load_16(st_h + 32u * (uint32_t)slot, row + coff - 4, bar);
+    if (has_r) bulk_load_16(st_h + 32u * (uint32_t)slot + 16u, row + coff + rowf, bar);
+  };
   if (tid < 32 && jb < je) {
-    if (lane == 0) mbar_arrive_expect_tx(bar, 4u * rowb);
+    if (lane == 0) mbar_arrive_expect_tx(bar, 4u * rowb + halo_bytes(jb - 1) + halo_bytes(jb) + halo_bytes(jb + 1));
     __syncwarp();
     load_u(jb - 1, 0);
     load_u(jb, 1);
     load_u(jb + 1, 2);
     load_m(jb);
+    if (lane == 0) {
+      load_halo(jb - 1, 0);
+      load_halo(jb, 1);
+      load_halo(jb + 1, 2);
+    }
   }
   const int li0 = tid * K;          // first unknown of this thread within the part
   const int i0 = coff + li0;        // ... and within the row
@@ -480,10 +505,12 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
       for (int k = 0; k < K; ++k) d[k] += v[k];
       stage_vec<K>(uc, uc_row, li0);
       stage_vec<K>(v, sm, li0);
-      // neighbours across the split between the CTAs of a cluster come from L2
-      const size_t rowg = (size_t)j * a.ld;
-      const float uL = (i0 > 0) ? (li0 > 0 ? stage_at(uc_row, li0 - 1) : __ldg(a.u + rowg + i0 - 1)) : 0.f;
-      const float uR = (i0 + K < a.nx) ? (li0 + K < rowf ? stage_at(uc_row, li0 + K) : __ldg(a.u + rowg + i0 + K)) : 0.f;
+      // neighbours across the split between the CTAs of a cluster: the
+      // row's halo groups (element coff - 1 ends the left one, coff + rowf
+      // starts the right one)
+      const float* hs = sh + 8 * sc;
+      const float uL = (i0 > 0) ? (li0 > 0 ? stage_at(uc_row, li0 - 1) : hs[3]) : 0.f;
+      const float uR = (i0 + K < a.nx) ? (li0 + K < rowf ? stage_at(uc_row, li0 + K) : hs[4]) : 0.f;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const float c = uc[k];
@@ -513,10 +540,11 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
     __syncthreads();                 // slot of row j - 1 and the m stage are consumed
     if (tid < 32 && j + 1 < je) {
       fence_proxy_async_smem();
-      if (lane == 0) mbar_arrive_expect_tx(bar, 2u * rowb);
+      if (lane == 0) mbar_arrive_expect_tx(bar, 2u * rowb + halo_bytes(j + 2));
       __syncwarp();
       load_u(j + 2, sp);
       load_m(j + 1);
+      if (lane == 0) load_halo(j + 2, sp);
     }
     x_solve_row_async<K, XC>(smem, rank, r, d, s, timed_out);
     // w through the swizzled stage, stored by TMA boxes
@@ -1008,9 +1036,9 @@ static cudaError_t launch_x_pipe_t(const XArgs& a_in, const CUtensorMap& tu, con
   return cudaLaunchKernelEx(&cfg, x_pipe_kernel<K, MAXT, XC>, a, tu, tm, tw);
 }
 
-// Band form: [XSplitSmem] [mbarrier] [pad to 1024] [u ring 3 x rowf] [m rowf] [w rowf].
+// Band form: [XAsyncSmem] [mbarrier] [pad to 1024] [u ring 3 x rowf] [m rowf] [w rowf] [halo 96 B].
 size_t x_band_smem_bytes(int tsys, int K, int xc) {
-  return align64(XAsyncSmem::bytes(std::max(1, tsys / 32), xc)) + 8 + 1024 + (size_t)5 * tsys * K * 4;
+  return align64(XAsyncSmem::bytes(std::max(1, tsys / 32), xc)) + 8 + 1024 + (size_t)5 * tsys * K * 4 + 128;
 }
 
 template <int K, int MAXT, int XC>

@@ -79,6 +79,15 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm,
       : "memory");
 }
 
+// Untiled bulk copy of 16 bytes from global to this CTA's shared memory,
+// completing on an mbarrier (both addresses 16-byte aligned).
+__device__ __forceinline__ void bulk_load_16(uint32_t dst, const void* src, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], 16, [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(src)), "r"(bar)
+      : "memory");
+}
+
 // Tiled 2D tensor load (coordinates in elements, innermost first; c0 * 4
 // bytes a multiple of 16; dst 128-byte aligned).
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int c0, int c1,
