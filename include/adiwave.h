@@ -61,7 +61,7 @@ enum {
     ADI_ENUMERIC = 4,    /* a non-finite value was produced (device flag) */
     ADI_ETIMEOUT = 5,    /* a bounded device-side wait expired (device flag) */
     ADI_ESTATE = 6,      /* call not valid in the handle's state */
-    ADI_EUNSUPPORTED = 7 /* valid request this build does not implement */
+    ADI_EUNSUPPORTED = 7 /* valid request the library does not implement for this shape or mode */
 };
 
 enum { ADI_START_PAPER = 0,     /* Eq. (CN2): u^1 = phi + tau psi */

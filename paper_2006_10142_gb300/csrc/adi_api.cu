@@ -303,7 +303,7 @@ extern "C" const char* adi_wave_strerror(int code) {
     case ADI_ENUMERIC: return "non-finite value produced";
     case ADI_ETIMEOUT: return "bounded device wait expired";
     case ADI_ESTATE: return "call not valid in the handle's state";
-    case ADI_EUNSUPPORTED: return "not supported by this build";
+    case ADI_EUNSUPPORTED: return "not supported for this shape or mode";
     default: return "unknown error code";
   }
 }
