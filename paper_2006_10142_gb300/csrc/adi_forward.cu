@@ -388,6 +388,99 @@ __device__ __forceinline__ void x_solve_row_async(unsigned char* smem, int rank,
 }
 
 // ---------------------------------------------------------------------------
+// Column solves of the pipelined y sweep (one group of tcol <= 32 threads
+// per column and CTA) with the CTAs of a cluster exchanging their column
+// summaries by st.async instead of cluster barriers: every CTA sends the
+// summary of its segment of each column to every CTA of the cluster, into
+// buffer r & 1 of strip r, completing on the receiver's mbarrier, and
+// solves the strip's W top systems itself.  A CTA writes strip r + 2's
+// summaries only after it has received every CTA's strip r + 1 summaries,
+// which those CTAs send after reading their strip r buffer, so the two
+// buffers never race.
+// Shared memory: [YTreeSmem csum | nodes] [tops: 2][W][C] [bars: 2].
+// ---------------------------------------------------------------------------
+struct YAsyncSmem {
+  static __host__ __device__ size_t off_tops(int threads) { return YTreeSmem<float>::off_tops(threads); }
+  static __host__ __device__ size_t off_bars(int threads, int W, int C) {
+    return off_tops(threads) + align64((size_t)2 * W * C * sizeof(Seg<float>));
+  }
+  static __host__ __device__ size_t bytes(int threads, int W, int C) { return off_bars(threads, W, C) + 64; }
+};
+
+template <int K>
+__device__ __forceinline__ void y_solve_cols_async(unsigned char* smem, int W, int log2tcol, int C, int rank,
+                                                   int col, int q, int r, float (&d)[K], float (&s)[K],
+                                                   bool& timed_out) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int threads = blockDim.x;
+  const int lg = log2tcol;  // tree levels (tcol <= 32)
+  const int tcol = 1 << lg;
+  const int cpw = 32 >> lg;  // columns whose trees one warp holds
+  Seg<float>* csum = reinterpret_cast<Seg<float>*>(smem);
+  Node<float>* nodes = reinterpret_cast<Node<float>*>(smem + YTreeSmem<float>::off_nodes(threads)) + warp * 31;
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  const int b = r & 1;
+  const size_t toff = YAsyncSmem::off_tops(threads) + (size_t)b * W * C * sizeof(Seg<float>);
+  const uint32_t tops_a = sa + (uint32_t)toff;
+  const Seg<float>* tops = reinterpret_cast<const Seg<float>*>(smem + toff);
+  const uint32_t bar = sa + (uint32_t)YAsyncSmem::off_bars(threads, W, C) + 8u * (uint32_t)b;
+  Node<float> ndc;
+  {
+    Seg<float> S;
+    chunk_reduce_split<K, float>(d, s, S, ndc);
+    csum[col * tcol + q] = S;
+  }
+  __syncthreads();
+  const int tc = warp * cpw + (lane >> lg);  // column of this lane's tree
+  const int chunk = lane & (tcol - 1);
+  Seg<float> S = csum[tc * tcol + chunk];
+  S = warp_tree_up<float>(S, nodes, lane, lg);  // every lane of the group holds the column's summary
+  for (int dst = chunk; dst < C; dst += tcol) {
+    const uint32_t da = mapa_shared(tops_a + (uint32_t)((tc * C + rank) * sizeof(Seg<float>)), dst);
+    const uint32_t db = mapa_shared(bar, dst);
+    st_async_v4(da, S.f.a, S.f.b, S.f.c, S.f.d, db);
+    st_async_v4(da + 16u, S.l.a, S.l.b, S.l.c, S.l.d, db);
+  }
+  if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, (uint32_t)(W * C * sizeof(Seg<float>)));
+  const uint32_t par = (uint32_t)((r >> 1) & 1);
+  if (!mbar_try_wait_cluster(bar, par)) {
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait_cluster(bar, par)) {
+      if (global_ns() - t0 > 1000000000ull) {
+        timed_out = true;
+        break;
+      }
+    }
+  }
+  // the top systems of this warp's columns: lane l holds segment l's two
+  // equations; each group takes the end values of this CTA's segment
+  float xa = 0.f, xc = 0.f;
+  for (int j = 0; j < cpw; ++j) {
+    const int c = warp * cpw + j;
+    Eq<float> E0 = eq_identity<float>(), E1 = eq_identity<float>();
+    if (lane < C) {
+      E0 = tops[c * C + lane].f;
+      E1 = tops[c * C + lane].l;
+    }
+    pcr64<float>(E0, E1, lane, 2 * C);
+    const float x0 = __shfl_sync(0xffffffffu, div_t(E0.d, E0.b), rank);
+    const float x1 = __shfl_sync(0xffffffffu, div_t(E1.d, E1.b), rank);
+    if ((lane >> lg) == j) {
+      xa = x0;
+      xc = x1;
+    }
+  }
+  warp_tree_down<float>(nodes, lane, lg, xa, xc);
+  float* cx = reinterpret_cast<float*>(csum + tc * tcol + chunk);
+  cx[0] = xa;
+  cx[1] = xc;
+  __syncthreads();
+  const float* mine = reinterpret_cast<const float*>(csum + col * tcol + q);
+  chunk_backsub_split<K, float>(d, s, ndc, mine[0], mine[1]);
+}
+
+// ---------------------------------------------------------------------------
 // pass 1, band form (FP32, tree solver, K = 16 or 32, rows split over a
 // cluster of XC CTAs): each cluster walks a band of consecutive rows from top to bottom
 // and keeps a ring of three rows of u^k in shared memory (rows j - 1, j,
@@ -611,7 +704,7 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT)) y_sweep_kernel(const YAr
 // reciprocal per node); tm_uc and tm_up
 // are not used and nothing else is written.
 // ---------------------------------------------------------------------------
-template <int K, int MAXT, int W, bool ADJ>
+template <int K, int MAXT, int W, bool ADJ, bool XA>
 __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
     y_pipe_kernel(const YArgs a, const __grid_constant__ CUtensorMap tm_w,
                   const __grid_constant__ CUtensorMap tm_m, const __grid_constant__ CUtensorMap tm_uc,
@@ -638,9 +731,15 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
 
   if (tid == 0) {
     mbar_init(bar, 1);
+    if (XA) {
+      const uint32_t xb = sa + (uint32_t)YAsyncSmem::off_bars((int)blockDim.x, W, C);
+      mbar_init(xb, 1);
+      mbar_init(xb + 8u, 1);
+    }
     mbar_fence_init();
   }
   __syncthreads();
+  if (XA) cgx::this_cluster().sync();  // every CTA's summary barriers exist before the first st.async
   // warp 0: copies of strip `st` (this CTA's rows) and L2 prefetch of its
   // u boxes, one box per lane
   const int lane = tid & 31;
@@ -673,8 +772,9 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
   bool timed_out = false;
   bool bad = false;
   const float sc = (float)a.sc;
-  for (; strip < nstrips; strip += ncl) {
-    cluster_arrive_early(C);
+  int r = 0;  // strips this cluster has solved
+  for (; strip < nstrips; strip += ncl, ++r) {
+    if (!XA) cluster_arrive_early(C);
     const int i = strip * W + col;
     const bool colok = i < a.nx;
     if (!mbar_wait_bounded(bar, phase, 1000000000ull)) timed_out = true;
@@ -719,9 +819,13 @@ __global__ void __launch_bounds__(MAXT, min_ctas(MAXT))
       fence_proxy_async_smem();
       issue(next);
     }
-    // the cluster barrier at the top of the next strip keeps the owners'
-    // shared memory alive until every remote read is done
-    y_solve_cols<K, float, true>(smem, a.log2W, a.log2tcol, C, rank, a.pcr, col, gq, d, s, false);
+    if (XA) {
+      y_solve_cols_async<K>(smem, W, a.log2tcol, C, rank, col, q, r, d, s, timed_out);
+    } else {
+      // the cluster barrier at the top of the next strip keeps the owners'
+      // shared memory alive until every remote read is done
+      y_solve_cols<K, float, true>(smem, a.log2W, a.log2tcol, C, rank, a.pcr, col, gq, d, s, false);
+    }
     if (ADJ) {
       if (colok) {
         const size_t base = (size_t)j0 * ld + i;
@@ -1105,7 +1209,14 @@ cudaError_t launch_x_pipe(const XArgs& a, int K, const CUtensorMap& tu, const CU
   return cudaErrorInvalidValue;
 }
 
-static size_t y_pipe_tree_bytes(int W, int C, int tcol) { return y_smem_bytes(W, C, tcol, false, true); }
+// The st.async exchange needs a cluster, one group per column (tcol <= 32)
+// and at most 32 segments (one warp's top system).
+static bool y_pipe_async_ok(int C, int tcol) { return C > 1 && tcol <= 32 && C <= 32; }
+
+static size_t y_pipe_tree_bytes(int W, int C, int tcol) {
+  const size_t t = y_smem_bytes(W, C, tcol, false, true);
+  return y_pipe_async_ok(C, tcol) ? std::max(t, YAsyncSmem::bytes(W * tcol, W, C)) : t;
+}
 
 size_t y_pipe_smem_bytes(int W, int C, int tcol, int K) {
   const size_t R = (size_t)tcol * K;
@@ -1159,11 +1270,13 @@ static cudaError_t launch_y_pipe_t(const YArgs& a_in, const YMaps& mp, cudaStrea
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  const bool xa = y_pipe_async_ok(a.C, tcol);
+  auto kern = xa ? y_pipe_kernel<K, MAXT, W, ADJ, true> : y_pipe_kernel<K, MAXT, W, ADJ, false>;
   int nc = 0;
-  cudaError_t e = cudaOccupancyMaxActiveClusters(&nc, y_pipe_kernel<K, MAXT, W, ADJ>, &cfg);
+  cudaError_t e = cudaOccupancyMaxActiveClusters(&nc, kern, &cfg);
   if (e != cudaSuccess) return e;
   cfg.gridDim = dim3(std::max(1, std::min(strips, nc)) * a.C, 1, 1);
-  return cudaLaunchKernelEx(&cfg, y_pipe_kernel<K, MAXT, W, ADJ>, a, mp.w, mp.m, mp.uc, mp.up);
+  return cudaLaunchKernelEx(&cfg, kern, a, mp.w, mp.m, mp.uc, mp.up);
 }
 
 // 16-column strips (narrower strips, which fit smaller clusters, measured
@@ -1276,14 +1389,22 @@ cudaError_t configure_kernels() {
   ADI_CFG_SMALL(x_sweep_kernel, false, false)
   ADI_CFG_SMALL(y_sweep_kernel, true, true)
   ADI_CFG_SMALL(y_sweep_kernel, false, true)
-  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<16, 256, 16, false>, true);
-  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<16, 256, 16, true>, true);
-  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<16, 512, 16, false>, true);
-  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<16, 512, 16, true>, true);
-  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<32, 256, 16, false>, true);
-  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<32, 256, 16, true>, true);
-  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<32, 512, 16, false>, true);
-  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<32, 512, 16, true>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<16, 256, 16, false, false>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<16, 256, 16, false, true>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<16, 256, 16, true, false>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<16, 256, 16, true, true>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<16, 512, 16, false, false>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<16, 512, 16, false, true>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<16, 512, 16, true, false>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<16, 512, 16, true, true>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<32, 256, 16, false, false>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<32, 256, 16, false, true>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<32, 256, 16, true, false>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<32, 256, 16, true, true>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<32, 512, 16, false, false>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<32, 512, 16, false, true>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<32, 512, 16, true, false>, true);
+  if (e == cudaSuccess) e = allow_smem(y_pipe_kernel<32, 512, 16, true, true>, true);
   if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<8, 1024, 1>, false);
   if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<16, 256, 1>, false);
   if (e == cudaSuccess) e = allow_smem(x_pipe_kernel<16, 512, 1>, false);
