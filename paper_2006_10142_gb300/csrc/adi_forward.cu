@@ -1209,9 +1209,10 @@ cudaError_t launch_x_pipe(const XArgs& a, int K, const CUtensorMap& tu, const CU
   return cudaErrorInvalidValue;
 }
 
-// The st.async exchange needs a cluster, one group per column (tcol <= 32)
-// and at most 32 segments (one warp's top system).
-static bool y_pipe_async_ok(int C, int tcol) { return C > 1 && tcol <= 32 && C <= 32; }
+// The st.async exchange needs one group per column (tcol <= 32) and at most
+// 32 segments (one warp's top system); it is taken for clusters of 4 CTAs
+// or more, whose barriers span more SMs (pairs keep the barrier form).
+static bool y_pipe_async_ok(int C, int tcol) { return C >= 4 && tcol <= 32 && C <= 32; }
 
 static size_t y_pipe_tree_bytes(int W, int C, int tcol) {
   const size_t t = y_smem_bytes(W, C, tcol, false, true);
